@@ -1,0 +1,227 @@
+"""FP64 CPU oracle of the TSBTS integrator (Kaplan & Saygin, Sec. 2-4).
+
+TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the bench's
+CPU-baseline leg may import this package. It is built from the plain C in
+``tsbts_oracle.c`` with gcc and shares nothing with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tsbts_oracle.c")
+_HDR = os.path.join(_HERE, "tsbts_oracle.h")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_SO = os.path.join(_LIBDIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+I64 = C.c_int64
+I32P = C.POINTER(C.c_int32)
+I64P = C.POINTER(C.c_int64)
+DP = C.POINTER(C.c_double)
+
+
+class OrcCfg(C.Structure):
+    _fields_ = [("n_iter", C.c_int), ("era_mode", C.c_int),
+                ("era_log2", C.c_int), ("k_max", C.c_int),
+                ("dyn_min_log2", C.c_int), ("log", C.c_int),
+                ("eps", C.c_double), ("eta", C.c_double),
+                ("dt_max", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, OpenMP over bodies)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
+        return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_forces.argtypes = [I64, DP, DP, DP, C.c_double, I64, I32P,
+                                     DP, DP, DP]
+            L.orc_energy_of.argtypes = [I64, DP, DP, DP, C.c_double, DP, DP]
+            L.orc_level_ticks.argtypes = [C.c_double, C.c_int, C.c_int, I64P]
+            L.orc_level_ticks.restype = I64
+            L.orc_forward_step.argtypes = [I64, I64, C.c_double, C.c_int,
+                                           C.c_int, I64P]
+            L.orc_forward_step.restype = I64
+            L.orc_symmetric_step.argtypes = [I64, I64, C.c_double, C.c_double,
+                                             C.c_double, C.c_int, C.c_int, I64P]
+            L.orc_symmetric_step.restype = I64
+            L.orc_hermite.argtypes = [I64, I64, I64, C.c_int, DP, DP, DP, DP,
+                                      DP, DP, DP, DP]
+            L.orc_create.argtypes = [I64, DP, DP, DP, C.POINTER(OrcCfg)]
+            L.orc_create.restype = C.c_void_p
+            L.orc_run.argtypes = [C.c_void_p, C.c_double]
+            L.orc_run.restype = C.c_int
+            L.orc_energy.argtypes = [C.c_void_p, DP, DP]
+            L.orc_get_state.argtypes = [C.c_void_p, DP, DP, DP, I64P, I64P, DP]
+            L.orc_stats.argtypes = [C.c_void_p, I64P]
+            L.orc_log_steps.argtypes = [C.c_void_p]
+            L.orc_log_steps.restype = I64
+            L.orc_log_entries.argtypes = [C.c_void_p]
+            L.orc_log_entries.restype = I64
+            L.orc_log_get.argtypes = [C.c_void_p, I32P, I32P, I64P, I32P, I32P,
+                                      I64P]
+            L.orc_era_log.argtypes = [C.c_void_p, I64P, I64P]
+            L.orc_era_log.restype = I64
+            L.orc_destroy.argtypes = [C.c_void_p]
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _d(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _p(x, t=DP):
+    return x.ctypes.data_as(t)
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def forces(m, r, v, eps, idx=None):
+    """a (n_act, 3), phi (n_act,), q (n_act,) on bodies idx from all bodies."""
+    m, r, v = _d(m), _d(r), _d(v)
+    n = m.shape[0]
+    idx = np.arange(n, dtype=np.int32) if idx is None else \
+        np.ascontiguousarray(idx, dtype=np.int32)
+    na = idx.shape[0]
+    a = np.zeros((na, 3))
+    phi = np.zeros(na)
+    q = np.zeros(na)
+    lib().orc_forces(n, _p(m), _p(r), _p(v), float(eps), na, _p(idx, I32P),
+                     _p(a), _p(phi), _p(q))
+    return a, phi, q
+
+
+def energy_of(m, r, v, eps):
+    m, r, v = _d(m), _d(r), _d(v)
+    ek, ep = C.c_double(), C.c_double()
+    lib().orc_energy_of(m.shape[0], _p(m), _p(r), _p(v), float(eps),
+                        C.byref(ek), C.byref(ep))
+    return ek.value, ep.value
+
+
+def level_ticks(x, k_min, k_max):
+    uf = C.c_int64(0)
+    t = lib().orc_level_ticks(float(x), k_min, k_max, C.byref(uf))
+    return int(t), int(uf.value)
+
+
+def forward_step(tau, d, dts, k_min, k_max):
+    uf = C.c_int64(0)
+    t = lib().orc_forward_step(int(tau), int(d), float(dts), k_min, k_max,
+                               C.byref(uf))
+    return int(t), int(uf.value)
+
+
+def symmetric_step(tau, d, dts, dte_2d, dte_d, k_min, k_max):
+    uf = C.c_int64(0)
+    t = lib().orc_symmetric_step(int(tau), int(d), float(dts), float(dte_2d),
+                                 float(dte_d), k_min, k_max, C.byref(uf))
+    return int(t), int(uf.value)
+
+
+def hermite(ta, tb, t, k_max, ra, va, aa, rb, vb, ab):
+    ro, vo = np.zeros(3), np.zeros(3)
+    args = [_d(x) for x in (ra, va, aa, rb, vb, ab)]
+    lib().orc_hermite(int(ta), int(tb), int(t), int(k_max),
+                      *[_p(x) for x in args], _p(ro), _p(vo))
+    return ro, vo
+
+
+class Sim:
+    """One oracle integration (Alg. 2 / Alg. 3) over seeded inputs."""
+
+    def __init__(self, m, r, v, *, eps, eta, dt_max, n_iter=3, era_mode=0,
+                 era_log2=3, k_max=20, dyn_min_log2=3, log=False):
+        self.m, r, v = _d(m), _d(r), _d(v)
+        self.n = self.m.shape[0]
+        self.k_max = k_max
+        cfg = OrcCfg(n_iter, era_mode, era_log2, k_max, dyn_min_log2,
+                     1 if log else 0, eps, eta, dt_max)
+        self._s = lib().orc_create(self.n, _p(self.m), _p(r), _p(v),
+                                   C.byref(cfg))
+
+    def run(self, t_end):
+        rc = lib().orc_run(self._s, float(t_end))
+        if rc != 0:
+            raise ValueError(f"oracle run refused t_end={t_end}")
+
+    def energy(self):
+        ek, ep = C.c_double(), C.c_double()
+        lib().orc_energy(self._s, C.byref(ek), C.byref(ep))
+        return ek.value, ep.value
+
+    def state(self):
+        n = self.n
+        r, v, a = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+        tau, dt = np.zeros(n, np.int64), np.zeros(n, np.int64)
+        dts = np.zeros(n)
+        lib().orc_get_state(self._s, _p(r), _p(v), _p(a), _p(tau, I64P),
+                            _p(dt, I64P), _p(dts))
+        return dict(r=r, v=v, a=a, tau=tau, dt=dt, dts=dts)
+
+    def stats(self):
+        out = np.zeros(7, np.int64)
+        lib().orc_stats(self._s, _p(out, I64P))
+        keys = ("block_steps", "interactions", "eras", "passes", "underflow",
+                "t_sys_ticks", "init_interactions")
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def schedule(self):
+        L = lib()
+        ns, ne = L.orc_log_steps(self._s), L.orc_log_entries(self._s)
+        era = np.zeros(ns, np.int32)
+        pas = np.zeros(ns, np.int32)
+        tau = np.zeros(ns, np.int64)
+        nact = np.zeros(ns, np.int32)
+        ei = np.zeros(ne, np.int32)
+        edt = np.zeros(ne, np.int64)
+        L.orc_log_get(self._s, _p(era, I32P), _p(pas, I32P), _p(tau, I64P),
+                      _p(nact, I32P), _p(ei, I32P), _p(edt, I64P))
+        return dict(era=era, pass_=pas, tau=tau, n_act=nact, idx=ei, dt=edt)
+
+    def eras(self):
+        L = lib()
+        ne = L.orc_era_log(self._s, None, None)
+        ts, te = np.zeros(ne, np.int64), np.zeros(ne, np.int64)
+        L.orc_era_log(self._s, _p(ts, I64P), _p(te, I64P))
+        return ts, te
+
+    def close(self):
+        if self._s:
+            lib().orc_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,99 @@
+/*
+ * FP64 CPU oracle of the time-symmetric block time-step (TSBTS) integrator
+ * with fixed or dynamic era (Kaplan & Saygin, Sec. 2-4).
+ *
+ * TEST INFRASTRUCTURE ONLY. This header and its implementation are the
+ * slow, plain reference that the CUDA library is checked against. Only the
+ * test suite, the smoke check and the bench's CPU-baseline leg may load it.
+ * It shares no code, header, table or helper with the CUDA library.
+ *
+ * Units: G = 1. Time is kept as integer ticks, 2^k_max ticks per time unit.
+ * Arrays of vectors are row-major (n, 3) doubles: x, y, z per body.
+ */
+#ifndef TSBTS_ORACLE_H
+#define TSBTS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Plummer-softened force, potential and time-step criterion on bodies
+ * idx[0..n_act) from all bodies j != i (Sec. 2 Eq. 3, Sec. 3 softening):
+ *   a_i   = sum_j m_j d_ij / s^3,  phi_i = -sum_j m_j / s,
+ *   q_i   = max_j max(|v_ij|^2 / s^2, m_j / s^3),
+ * with d_ij = r_j - r_i and s^2 = |d_ij|^2 + eps^2. The time-step estimate
+ * of Eq. 3 is then eta / sqrt(q_i). j runs in ascending order. */
+void orc_forces(int64_t n, const double* m, const double* r, const double* v,
+                double eps, int64_t n_act, const int32_t* idx,
+                double* a, double* phi, double* q);
+
+/* Kinetic and softened potential energy of a state (Sec. 3 energy error). */
+void orc_energy_of(int64_t n, const double* m, const double* r,
+                   const double* v, double eps, double* ekin, double* epot);
+
+/* Largest power-of-two step 2^-k <= x with k_min <= k <= k_max, in ticks
+ * (Eq. 4). Below 2^-k_max it returns 1 tick and increments *underflow. */
+int64_t orc_level_ticks(double x, int k_min, int k_max, int64_t* underflow);
+
+/* First-pass (standard block step) choice of the next step. */
+int64_t orc_forward_step(int64_t tau, int64_t d, double dts, int k_min,
+                         int k_max, int64_t* underflow);
+
+/* Symmetrised choice of the next step (Alg. 1 and its prose), given the
+ * start-of-step estimate dts and the previous pass's estimates at the two
+ * candidate end times tau + 2d and tau + d. */
+int64_t orc_symmetric_step(int64_t tau, int64_t d, double dts, double dte_2d,
+                           double dte_d, int k_min, int k_max,
+                           int64_t* underflow);
+
+/* Time-symmetric cubic Hermite interpolation between two stored records
+ * at ticks ta < tb, evaluated at tick t (ta <= t <= tb). */
+void orc_hermite(int64_t ta, int64_t tb, int64_t t, int k_max,
+                 const double* ra, const double* va, const double* aa,
+                 const double* rb, const double* vb, const double* ab,
+                 double* r_out, double* v_out);
+
+typedef struct {
+  int n_iter;        /* passes per era (1 = plain block steps) */
+  int era_mode;      /* 0 fixed, 1 dynamic */
+  int era_log2;      /* fixed era = 2^-era_log2 time units */
+  int k_max;         /* smallest step 2^-k_max; ticks per unit = 2^k_max */
+  int dyn_min_log2;  /* dynamic era lower limit = dt_max * 2^-dyn_min_log2 */
+  int log;           /* record the block schedule */
+  double eps, eta, dt_max;
+} orc_cfg;
+
+typedef struct orc_sim orc_sim;
+
+orc_sim* orc_create(int64_t n, const double* m, const double* r,
+                    const double* v, const orc_cfg* cfg);
+/* Integrate whole eras until the system time reaches t_end. Returns 0, or
+ * -1 if t_end is not a whole number of ticks or lies in the past. */
+int orc_run(orc_sim* s, double t_end);
+/* Energy at the system time; bodies behind it are Taylor-predicted (Eq. 2). */
+void orc_energy(orc_sim* s, double* ekin, double* epot);
+void orc_get_state(orc_sim* s, double* r, double* v, double* a, int64_t* tau,
+                   int64_t* dt, double* dts);
+/* stats: [0] block steps, [1] interactions (sum n_act * n), [2] eras,
+ * [3] passes, [4] step underflows, [5] system time in ticks,
+ * [6] initial interactions */
+void orc_stats(orc_sim* s, int64_t* out);
+int64_t orc_log_steps(orc_sim* s);
+int64_t orc_log_entries(orc_sim* s);
+/* per block step: era index, pass, tau_next, n_act; per active body, in
+ * ascending index within its step: body index and new step in ticks */
+void orc_log_get(orc_sim* s, int32_t* step_era, int32_t* step_pass,
+                 int64_t* step_tau, int32_t* step_nact, int32_t* ent_i,
+                 int64_t* ent_dt);
+/* era bounds [tau_s, tau_e] in ticks, in order; returns the era count
+ * (pass NULL pointers to query the count) */
+int64_t orc_era_log(orc_sim* s, int64_t* tau_s, int64_t* tau_e);
+void orc_destroy(orc_sim* s);
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
