@@ -1,0 +1,415 @@
+"""Benchmark of the TSBTS hot path on GB300: G pair-interactions/s.
+
+Workload (one "step"): a Plummer sphere of n = 16384 equal-mass bodies in
+standard N-body units, eps = 1/256, eta = 0.01, dt = 2^-k (k = 3..20),
+dynamic era (Alg. 3), three passes per era, integrated over t = 0..1 from
+its initial conditions, mixed precision (FP32 pair terms, FP64 state).
+Interactions = sum over all block steps of all passes of n_act * n.
+
+JSON line keys beyond the driver contract:
+  roofline      force kernel vs the FP32 FMA-pipe bound (20 FMA-pipe ops
+                per interaction; 152 SMs x 128 lanes x clock)
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
+  fp64          the plain FP64 GPU path on a bounded sample
+  accuracy      relative energy errors of the GPU paths and the oracle on
+                the sample interval (bar: GPU <= 2x oracle)
+Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BODIES = 16384
+EPS = 1.0 / 256.0
+ETA = 0.01
+DT_MAX = 1.0 / 8.0
+T_END = 1.0
+N_ITER = 3
+SEED = 0
+SAMPLE_T = 2.0 ** -8        # oracle / FP64 sample interval
+OPS_PER_INTERACTION = 20    # FMA-pipe ops of the algorithmic pair term
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+METRIC = ("G pair-interactions/s, mixed vs FP64 on same GB300 at "
+          "|dE/E|<=2x oracle; steps/s")
+WORKLOAD = "plummer16384_eps1-256_eta0.01_dynamic_era_3iter_t0-1"
+
+
+def config_dict(extra=None):
+    c = {"workload": WORKLOAD, "n": N_BODIES, "eps": EPS, "eta": ETA,
+         "dt_max": DT_MAX, "k_range": [3, 20], "era": "dynamic",
+         "n_iter": N_ITER, "t_end": T_END, "seed": SEED,
+         "ic": "Plummer (Aarseth-Henon-Wielen), standard units",
+         "l2": "256 MiB buffer written between timed steps"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None,
+                    "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("gloo")
+    return dist
+
+
+def barrier(dist):
+    if dist:
+        dist.barrier()
+
+
+def reduce_max(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample(m, r, v, t_end, threads):
+    """The FP64 oracle on [0, t_end]: (interactions, seconds, dE/E)."""
+    import oracle
+    oracle.set_threads(threads)
+    s = oracle.Sim(m, r, v, eps=EPS, eta=ETA, dt_max=DT_MAX, n_iter=N_ITER,
+                   era_mode=1, era_log2=3, k_max=20)
+    e0 = sum(s.energy())
+    t0 = time.perf_counter()
+    s.run(t_end)
+    sec = time.perf_counter() - t0
+    de = abs(sum(s.energy()) / e0 - 1.0)
+    st = s.stats()
+    s.close()
+    return st["interactions"], sec, de, st["block_steps"]
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 CPU oracle, timed as it stands."""
+    if rank != 0:
+        return 0
+    from paper_1205_2288_gb300 import inputs
+    threads = os.cpu_count() or 1
+    m, r, v = inputs.plummer(N_BODIES, SEED)
+    tstep = 2.0 ** -9
+    for _ in range(args.warmup):
+        oracle_sample(m, r, v, tstep, threads)
+    tot_i, tot_s, steps = 0, 0.0, 0
+    for _ in range(args.steps):
+        i, s, de, bs = oracle_sample(m, r, v, tstep, threads)
+        tot_i += i
+        tot_s += s
+        steps += bs
+    value = tot_i / tot_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "Ginteractions/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": config_dict({"t_end": tstep, "precision": "fp64",
+                               "sample": f"t=0..{tstep} per step"}),
+        "block_steps_per_s": steps / tot_s,
+        "cpu_baseline": {"kind": "oracle", "cores": threads, "value": value,
+                         "unit": "Ginteractions/s",
+                         "sample": f"t=0..2^-9 of the workload per step"},
+        "e2e": {"value": value, "unit": "Ginteractions/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--t-end", type=float, default=T_END)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    dist = init_dist(ws)
+    if args.impl == "reference":
+        rc = run_reference(args, ws, rank)
+        if dist:
+            dist.destroy_process_group()
+        return rc
+
+    import numpy as np
+    import torch
+
+    from paper_1205_2288_gb300 import inputs, tsbts
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    t_end = args.t_end
+    m, r, v = inputs.plummer(N_BODIES, SEED + rank)
+    dm = torch.from_numpy(m).to(dev)
+    dr = torch.from_numpy(r).to(dev)
+    dv = torch.from_numpy(v).to(dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    cfg = tsbts.tsbts_config_default()
+    cfg.precision = tsbts.TSBTS_MIXED
+    cfg.n_iter = N_ITER
+    cfg.era_mode = 1
+    cfg.k_max = 20
+    cfg.device = local
+    cfg.stream = stream.cuda_stream
+    ctx = tsbts.tsbts_create(cfg)
+
+    def one_step(timing):
+        tsbts.tsbts_init_device(ctx, dm, dr, dv, EPS, ETA, DT_MAX)
+        tsbts.tsbts_set_timing(ctx, timing)
+        tsbts.tsbts_step_era(ctx, t_end)
+        return tsbts.tsbts_get_stats(ctx)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step(False)
+        # timed region: K full integrations, inputs resident in HBM
+        sampler = ClockSampler(local)
+        tot_inter = tot_steps = tot_launch = 0
+        force_ms = 0.0
+        force_launches = 0
+        elapsed_ms = 0.0
+        barrier(dist)
+        torch.cuda.synchronize()
+        sampler.start()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            st = one_step(True)
+            ev1.record(stream)
+            ev1.synchronize()
+            elapsed_ms += ev0.elapsed_time(ev1)
+            tot_inter += st["interactions"]
+            tot_steps += st["block_steps"]
+            tot_launch += st["kernel_launches"]
+            force_ms += st["force_ms"]
+            force_launches += st["force_launches"]
+        torch.cuda.synchronize()
+        barrier(dist)
+        clocks = sampler.stop()
+        de_mixed_full = None
+        ek, ep, _ = tsbts.tsbts_energy(ctx)
+        tsbts.tsbts_init_device(ctx, dm, dr, dv, EPS, ETA, DT_MAX)
+        e0 = sum(tsbts.tsbts_energy(ctx)[:2])
+        de_mixed_full = abs((ek + ep) / e0 - 1.0)
+
+        # end to end through the public API with host buffers
+        e2e_s = 0.0
+        e2e_inter = 0
+        pin = {k: torch.from_numpy(x).pin_memory() for k, x in
+               dict(m=m, r=r, v=v).items()}
+        h2d = 7 * 8 * N_BODIES
+        d2h = 6 * 8 * N_BODIES
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tsbts.tsbts_init(ctx, pin["m"].numpy(), pin["r"].numpy(),
+                             pin["v"].numpy(), EPS, ETA, DT_MAX)
+            tsbts.tsbts_step_era(ctx, t_end)
+            out = tsbts.tsbts_state(ctx, N_BODIES)
+            e2e_s += time.perf_counter() - t0
+            e2e_inter += tsbts.tsbts_get_stats(ctx)["interactions"]
+            assert np.isfinite(out["r"]).all()
+
+    sec = elapsed_ms / 1e3
+    sec_max = reduce_max(dist, sec)
+    inter_all = reduce_sum(dist, tot_inter)
+    value = inter_all / sec_max / 1e9
+    e2e_value = reduce_sum(dist, e2e_inter) / reduce_max(dist, e2e_s) / 1e9
+
+    line = None
+    if rank == 0:
+        clk = clocks.get("sm_mhz") or None
+        peak_max = SM_COUNT * FP32_LANES_PER_SM * 2070e6 / OPS_PER_INTERACTION
+        achieved = tot_inter / (force_ms / 1e3) if force_ms > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved / 1e9,
+                "peak": peak_max / 1e9, "unit": "Ginteractions/s",
+                "frac": achieved / peak_max, "traffic": None,
+                "kernel": "force_mixed_kernel",
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz / 20 "
+                              "FMA-pipe ops per interaction",
+                "force_launches": force_launches,
+                "force_ms_per_launch": force_ms / max(force_launches, 1)}
+        if clk:
+            roof["frac_at_measured_clock"] = achieved / (
+                SM_COUNT * FP32_LANES_PER_SM * clk * 1e6 / OPS_PER_INTERACTION)
+        line = {
+            "metric": METRIC, "value": value, "unit": "Ginteractions/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": config_dict({"precision": "mixed", "t_end": t_end,
+                                   "parallelism": f"replicas{ws}"}),
+            "block_steps_per_s": tot_steps / sec,
+            "interactions_per_step": tot_inter / args.steps,
+            "gpu_launches": tot_launch,
+            "e2e": {"value": e2e_value, "unit": "Ginteractions/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "roofline": roof,
+            "clocks": clocks,
+            "accuracy": {"dE_E_mixed_t_end": de_mixed_full},
+        }
+
+    tsbts.tsbts_destroy(ctx)
+
+    if rank == 0:
+        # the plain FP64 GPU path on a bounded sample of the same workload
+        if not args.no_fp64:
+            cfg64 = tsbts.tsbts_config_default()
+            cfg64.precision = tsbts.TSBTS_FP64
+            cfg64.n_iter = N_ITER
+            cfg64.era_mode = 1
+            cfg64.device = local
+            sim = tsbts.Simulation(m, r, v, eps=EPS, eta=ETA, dt_max=DT_MAX,
+                                   precision=tsbts.TSBTS_FP64, n_iter=N_ITER,
+                                   era_mode=1, device=local)
+            e0 = sum(sim.energy())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.step_era(SAMPLE_T)
+            s64 = time.perf_counter() - t0
+            st = sim.stats()
+            de64 = abs(sum(sim.energy()) / e0 - 1.0)
+            sim.close()
+            mixed = tsbts.Simulation(m, r, v, eps=EPS, eta=ETA, dt_max=DT_MAX,
+                                     precision=tsbts.TSBTS_MIXED,
+                                     n_iter=N_ITER, era_mode=1, device=local)
+            e0m = sum(mixed.energy())
+            mixed.step_era(SAMPLE_T)
+            dem = abs(sum(mixed.energy()) / e0m - 1.0)
+            mixed.close()
+            line["fp64"] = {"value": st["interactions"] / s64 / 1e9,
+                            "unit": "Ginteractions/s",
+                            "sample": f"t=0..{SAMPLE_T} (wall clock)",
+                            "speedup_mixed_over_fp64":
+                                value / (st["interactions"] / s64 / 1e9)}
+            line["accuracy"].update({"t_sample": SAMPLE_T,
+                                     "dE_E_fp64_gpu": de64,
+                                     "dE_E_mixed_gpu": dem})
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            oi, osec, ode, obs = oracle_sample(m, r, v, SAMPLE_T, threads)
+            line["cpu_baseline"] = {
+                "value": oi / osec / 1e9, "unit": "Ginteractions/s",
+                "cores": threads, "kind": "oracle",
+                "sample": f"t=0..{SAMPLE_T} of the workload ({oi} "
+                          f"interactions, {osec:.1f} s)"}
+            line["accuracy"]["dE_E_oracle"] = ode
+            if "dE_E_mixed_gpu" in line["accuracy"]:
+                acc = line["accuracy"]
+                acc["mixed_within_2x_oracle"] = bool(
+                    acc["dE_E_mixed_gpu"] <= 2 * ode + 1e-12)
+        print(json.dumps(line), flush=True)
+    if dist:
+        barrier(dist)
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * tsbts.h - C ABI of the GB300 (sm_103a) library for the era-based
+ * time-symmetric block time-step (TSBTS) N-body integrator of Kaplan &
+ * Saygin ("A Dynamic Era-Based Time-Symmetric Block Time-Step Algorithm
+ * with Parallel Implementations"), Sec. 2-4.
+ *
+ * Conventions shared by every entry point:
+ *  - Units: G = 1. Times are doubles in N-body time units; internally
+ *    every time is an integer tick count, 2^k_max ticks per time unit.
+ *  - Vectors are row-major (n, 3) float64 arrays: x, y, z per body.
+ *  - Inputs are copied; the library never frees caller memory and keeps
+ *    no pointer to it after the call returns.
+ *  - Every call returns a tsbts_status. No C++ exception and no CUDA error
+ *    crosses this boundary. After TSBTS_ERR_CUDA, TSBTS_ERR_NONFINITE or
+ *    TSBTS_ERR_TIMEOUT a context is poisoned: further calls on it return
+ *    TSBTS_ERR_STATE until tsbts_destroy. tsbts_last_error gives a message.
+ *  - A context is used by one host thread at a time.
+ *  - The library has no CPU fallback: without a usable CUDA device,
+ *    tsbts_create returns TSBTS_ERR_CUDA.
+ */
+#ifndef TSBTS_H
+#define TSBTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TSBTS_OK = 0,
+  TSBTS_ERR_ARG = -1,        /* invalid argument; nothing was changed */
+  TSBTS_ERR_CUDA = -2,       /* CUDA runtime error (context poisoned) */
+  TSBTS_ERR_NONFINITE = -3,  /* non-finite input or force (poisoned) */
+  TSBTS_ERR_TIMEOUT = -4,    /* a bounded device wait gave up (poisoned) */
+  TSBTS_ERR_HISTORY = -6,    /* era history could not grow (no memory) */
+  TSBTS_ERR_STATE = -7       /* call out of order, or context poisoned */
+} tsbts_status;
+
+typedef enum { TSBTS_FP64 = 0, TSBTS_MIXED = 1 } tsbts_precision;
+
+/* Integrator settings (Sec. 3 "era size", Sec. 4 Alg. 3, Sec. 2 Alg. 2).
+ * tsbts_config_default fills the defaults listed beside each field. */
+typedef struct {
+  int precision;     /* tsbts_precision; default TSBTS_FP64.
+                        FP64: all pairwise arithmetic in FP64, rounded op by
+                        op in the order of the plain definition.
+                        MIXED: FP32 pairwise terms on double-single (hi+lo)
+                        relative coordinates, compensated FP32 sums folded
+                        per j-tile; FP64 positions, velocities, times and
+                        energy. */
+  int n_iter;        /* passes per era (Alg. 2 "iteration limit"); 1 = plain
+                        block steps; default 3 */
+  int era_mode;      /* 0 = fixed era (Sec. 3), 1 = dynamic era (Alg. 3);
+                        default 0 */
+  int era_log2;      /* fixed era = 2^-era_log2 time units, 0..k_max;
+                        default 3 */
+  int dyn_min_log2;  /* dynamic era lower limit = dt_max * 2^-dyn_min_log2;
+                        default 3 (Sec. 4 uses 2^-3 of the largest step) */
+  int k_max;         /* smallest step 2^-k_max, 1..40; default 20 */
+  int exact_order;   /* FP64 only: 1 = every force sum runs over j in
+                        ascending order in one thread (bit-identical to a
+                        sequential FP64 loop, slow for small active sets);
+                        0 = j-split across thread blocks with a fixed-order
+                        second stage (deterministic, different rounding);
+                        -1 = automatic: exact when n <= 8192. Default -1 */
+  int device;        /* CUDA device ordinal; default 0 */
+  void* stream;      /* cudaStream_t to run on, or NULL for a private
+                        stream owned by the context; default NULL */
+  int graph_steps;   /* block steps per captured CUDA graph launch; 0 = plain
+                        stream launches; default 32 */
+} tsbts_config;
+
+typedef struct tsbts_ctx tsbts_ctx;
+
+/* Counters of one context since tsbts_init. */
+typedef struct {
+  int64_t block_steps;    /* block steps over all passes */
+  int64_t interactions;   /* sum over block steps of n_act * n (the pairs
+                             evaluated, self pairs counted) */
+  int64_t eras;
+  int64_t passes;
+  int64_t dt_underflow;   /* steps clamped up to 2^-k_max */
+  int64_t era_restarts;   /* eras re-run after the history buffer grew */
+  int64_t history_capacity; /* records per pass buffer */
+  int64_t t_sys_ticks;    /* system time in ticks */
+  double force_ms;        /* device time in the force kernel, summed over
+                             launches when timing is on, else 0 */
+  int64_t force_launches;
+  int64_t kernel_launches;  /* kernels of this library launched by the
+                               context since tsbts_init */
+} tsbts_stats;
+
+void tsbts_config_default(tsbts_config* cfg);
+
+/* Create a context on cfg->device. Returns TSBTS_ERR_ARG for a bad config,
+ * TSBTS_ERR_CUDA if the device cannot be used. *out is NULL on error. */
+int tsbts_create(tsbts_ctx** out, const tsbts_config* cfg);
+
+/* Alg. 2 step 1: read the bodies, compute all forces and the first steps.
+ * m[n], r[n*3], v[n*3] are HOST pointers and are copied. eps >= 0 is the
+ * Plummer softening length (Sec. 3), eta > 0 the accuracy parameter of
+ * Eq. 3, dt_max = 2^-k (0 <= k <= k_max) the largest step. Sets the system
+ * time to 0. TSBTS_ERR_ARG: n < 1, a bad parameter, or dt_max not a power
+ * of two in range; TSBTS_ERR_NONFINITE: a non-finite input. */
+int tsbts_init(tsbts_ctx* ctx, int64_t n, const double* m, const double* r,
+               const double* v, double eps, double eta, double dt_max);
+
+/* Same as tsbts_init with DEVICE pointers (read on the context's stream
+ * before the call returns). */
+int tsbts_init_device(tsbts_ctx* ctx, int64_t n, const double* m_dev,
+                      const double* r_dev, const double* v_dev, double eps,
+                      double eta, double dt_max);
+
+/* Alg. 2 steps 2-11 (Alg. 3 for the dynamic era): integrate whole eras,
+ * each with n_iter passes, until the system time reaches t_end. t_end must
+ * be a whole number of ticks and not before the system time
+ * (TSBTS_ERR_ARG). The last era ends at t_end. *t_reached (may be NULL)
+ * receives the new system time. Bodies whose step overshoots an era end
+ * wait for a later era (Sec. 4), so body times may lag the system time.
+ * TSBTS_ERR_NONFINITE: a force or step estimate became non-finite;
+ * TSBTS_ERR_TIMEOUT: a pass stopped advancing the block time (both
+ * poison the context). */
+int tsbts_step_era(tsbts_ctx* ctx, double t_end, double* t_reached);
+
+/* Kinetic, softened potential and total energy at the system time (the
+ * relative energy error of Sec. 3 is formed from these). Bodies behind the
+ * system time are predicted with Eq. 2. Always FP64; the pair sum for each
+ * body runs in ascending j and the body sums in ascending i. */
+int tsbts_energy(tsbts_ctx* ctx, double* ekin, double* epot, double* etot);
+
+/* Copy the state to HOST buffers (each may be NULL): *t system time;
+ * m[n]; r, v, a [n*3] at each body's own time; tau_ticks[n] body times;
+ * dt_ticks[n] current steps. */
+int tsbts_state(tsbts_ctx* ctx, double* t, double* m, double* r, double* v,
+                double* a, int64_t* tau_ticks, int64_t* dt_ticks);
+
+int tsbts_get_stats(tsbts_ctx* ctx, tsbts_stats* out);
+
+/* Time every force launch with CUDA events (adds a small host cost per
+ * launch); the sum appears in tsbts_stats.force_ms. */
+int tsbts_set_timing(tsbts_ctx* ctx, int enable);
+
+/* Record the block schedule of the following calls: per block step the
+ * era index, pass, block time and active count, and per active body its
+ * index and new step. capacity_entries bounds the body entries (steps are
+ * bounded by the same number); 0 disables. Entries beyond capacity are
+ * dropped and counted. Active bodies of one step may be stored in any
+ * order. */
+int tsbts_schedule_log(tsbts_ctx* ctx, int64_t capacity_entries);
+/* Sizes of the recorded log; dropped counts entries that did not fit. */
+int tsbts_schedule_size(tsbts_ctx* ctx, int64_t* steps, int64_t* entries,
+                        int64_t* dropped);
+/* Copy the log to HOST arrays sized from tsbts_schedule_size. */
+int tsbts_schedule_get(tsbts_ctx* ctx, int32_t* step_era, int32_t* step_pass,
+                       int64_t* step_tau, int32_t* step_nact, int32_t* ent_i,
+                       int64_t* ent_dt);
+
+const char* tsbts_last_error(const tsbts_ctx* ctx);
+void tsbts_destroy(tsbts_ctx* ctx);
+
+/* Alg. 2 step 5 on its own (Sec. 2 Eq. 3, Sec. 3 softening): for each
+ * active body i = idx[k], k < n_act,
+ *   a[k]   = sum_{j != i} m_j d_ij / s^3,
+ *   phi[k] = -sum_{j != i} m_j / s,
+ *   q[k]   = max_{j != i} max(|v_ij|^2 / s^2, m_j / s^3),
+ * with d_ij = r_j - r_i, v_ij = v_j - v_i, s^2 = |d_ij|^2 + eps^2; the step
+ * estimate of Eq. 3 is eta / sqrt(q). All pointers are DEVICE pointers:
+ * m[n], r[n*3], v[n*3], idx[n_act] (int32, each in [0, n), repeats
+ * allowed), outputs a[n_act*3], phi[n_act], q[n_act] (caller-allocated).
+ * precision is a tsbts_precision; exact_order as in tsbts_config (FP64).
+ * Runs on `stream` (cudaStream_t, NULL = legacy default stream) and is
+ * asynchronous: outputs are ready when the stream reaches this point.
+ * Scratch memory (packed j records and j-split partial sums) is allocated
+ * by the library on first use per device, grown as needed and kept until
+ * tsbts_release_scratch. TSBTS_ERR_ARG: n < 1, n_act < 0, n or n_act above
+ * 2^31 - 1, or eps < 0. */
+int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
+                const double* r, const double* v, double eps, int64_t n_act,
+                const int32_t* idx, double* a, double* phi, double* q,
+                void* stream);
+
+/* Free the scratch memory of tsbts_force on the current device. */
+int tsbts_release_scratch(void);
+
+/* Library version string. */
+const char* tsbts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSBTS_H */

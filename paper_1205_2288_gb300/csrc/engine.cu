@@ -1,0 +1,900 @@
+// Host engine and C ABI of the TSBTS library (include/tsbts.h).
+//
+// One context owns the bodies, the era snapshot and two era-history
+// buffers in HBM, and drives Alg. 2 / Alg. 3 (Sec. 2, Sec. 4): eras, each
+// with n_iter passes restarted from the era-start snapshot, each pass a
+// device-resident loop of block steps. The host launches block steps in
+// chunks (stream launches or a captured CUDA graph of `graph_steps`
+// steps); kernels read the step state from the control block and return
+// once the pass is over, so the host synchronises once per chunk, not
+// once per block step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tsbts.h"
+#include "tsbts_kernels.cuh"
+
+using namespace tsbts;
+
+namespace {
+
+const char* kVersion = "tsbts-gb300 0.1 (sm_103a)";
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+inline void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw CudaFail{e, what};
+}
+
+}  // namespace
+
+struct tsbts_ctx {
+  tsbts_config cfg{};
+  std::string err;
+  bool poisoned = false;
+  bool inited = false;
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  int sms = 1;
+  // problem
+  int n = 0;
+  double eps = 0, eta = 0;
+  int k_min = 0;
+  long long dtmax_t = 0;
+  long long t_sys = 0;
+  int exact = 0;
+  // device memory
+  std::vector<void*> allocs;
+  Bodies B{}, snap{};
+  History H[2]{};
+  std::vector<void*> hist_allocs[2];
+  Params P{};
+  Ctl* d_ctl = nullptr;
+  Ctl* h_ctl = nullptr;  // pinned mirror
+  double* d_w = nullptr;
+  double* d_eout = nullptr;
+  int* d_nsplit = nullptr;  // scratch for init's split count
+  ForceLaunch fl{};
+  int correct_grid = 1;
+  // counters
+  long long eras = 0, passes = 0, restarts = 0;
+  long long max_rec = 0;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  double force_ms = 0;
+  long long force_launches = 0;
+  long long launches = 0;  // kernels launched since init
+  // schedule log
+  long long lg_cap = 0;
+  std::vector<void*> lg_allocs;
+  // CUDA graph of graph_steps block steps
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_dirty = true;
+};
+
+namespace {
+
+template <class T>
+T* dalloc(std::vector<void*>& list, size_t count) {
+  void* p = nullptr;
+  ck(cudaMalloc(&p, sizeof(T) * (count ? count : 1)), "cudaMalloc");
+  list.push_back(p);
+  return static_cast<T*>(p);
+}
+
+void free_list(std::vector<void*>& list) {
+  for (void* p : list) cudaFree(p);
+  list.clear();
+}
+
+int fail(tsbts_ctx* c, int code, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (code == TSBTS_ERR_CUDA || code == TSBTS_ERR_NONFINITE ||
+        code == TSBTS_ERR_TIMEOUT)
+      c->poisoned = true;
+  }
+  return code;
+}
+
+int cuda_fail(tsbts_ctx* c, const CudaFail& f) {
+  return fail(c, TSBTS_ERR_CUDA,
+              std::string(f.what) + ": " + cudaGetErrorString(f.e));
+}
+
+bool valid_dt_max(double dt_max, int k_max, int* k_min) {
+  for (int k = 0; k <= k_max; ++k)
+    if (std::ldexp(1.0, -k) == dt_max) {
+      *k_min = k;
+      return true;
+    }
+  return false;
+}
+
+void alloc_history(tsbts_ctx* c, int b, long long cap) {
+  free_list(c->hist_allocs[b]);
+  History& h = c->H[b];
+  auto& L = c->hist_allocs[b];
+  h.tau = dalloc<long long>(L, cap);
+  for (int d = 0; d < 3; ++d) {
+    h.r[d] = dalloc<double>(L, cap);
+    h.v[d] = dalloc<double>(L, cap);
+    h.a[d] = dalloc<double>(L, cap);
+  }
+  h.dts = dalloc<double>(L, cap);
+  h.next = dalloc<int>(L, cap);
+  h.cap = cap;
+  c->graph_dirty = true;
+}
+
+void release_graph(tsbts_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->graph_dirty = true;
+}
+
+void release_all(tsbts_ctx* c) {
+  release_graph(c);
+  if (c->s) cudaStreamSynchronize(c->s);
+  free_list(c->allocs);
+  free_list(c->hist_allocs[0]);
+  free_list(c->hist_allocs[1]);
+  free_list(c->lg_allocs);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  c->h_ctl = nullptr;
+  c->inited = false;
+}
+
+void read_ctl(tsbts_ctx* c) {
+  ck(cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                     c->s),
+     "read control block");
+  ck(cudaStreamSynchronize(c->s), "synchronize");
+}
+
+ForceArgs force_args_engine(tsbts_ctx* c, int p) {
+  ForceArgs fa{};
+  fa.n = c->n;
+  fa.m = c->B.m;
+  for (int d = 0; d < 3; ++d) {
+    fa.x[d] = c->B.pr[d];
+    fa.w[d] = c->B.pv[d];
+  }
+  fa.jhi = c->B.jhi;
+  fa.jlo = c->B.jlo;
+  fa.jv = c->B.jv;
+  fa.idx = c->B.act;
+  fa.n_act_fixed = -1;
+  fa.n_act_ptr = &c->d_ctl->slot[p].cnt;
+  fa.nsplit_out = &c->d_ctl->slot[p].nsplit;
+  fa.done = &c->d_ctl->done;
+  fa.part = c->B.part;
+  fa.part_cap = c->B.part_cap;
+  fa.eps2 = c->eps * c->eps;
+  fa.eps2f = (float)(c->eps * c->eps);
+  fa.exact = c->exact;
+  return fa;
+}
+
+// one block step: A (select + predict), B (force), C (correct)
+void enqueue_step(tsbts_ctx* c, int p, int ev_slot) {
+  const History& HA = c->H[0];
+  const History& HB = c->H[1];
+  launch_select_predict(c->B, c->P, HA, HB, p, c->s);
+  if (ev_slot >= 0) ck(cudaEventRecord(c->ev[2 * ev_slot], c->s), "event");
+  ck(launch_force(c->cfg.precision, force_args_engine(c, p), c->fl, c->s),
+     "force launch");
+  if (ev_slot >= 0) ck(cudaEventRecord(c->ev[2 * ev_slot + 1], c->s), "event");
+  launch_correct(c->B, c->P, HA, HB, p, c->correct_grid, c->s);
+}
+
+void ensure_events(tsbts_ctx* c, int steps) {
+  while ((int)c->ev.size() < 2 * steps) {
+    cudaEvent_t e;
+    ck(cudaEventCreate(&e), "cudaEventCreate");
+    c->ev.push_back(e);
+  }
+}
+
+void build_graph(tsbts_ctx* c) {
+  release_graph(c);
+  const int G = c->cfg.graph_steps;
+  if (c->timing) ensure_events(c, G);
+  cudaGraph_t g;
+  ck(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal),
+     "begin capture");
+  try {
+    for (int k = 0; k < G; ++k) enqueue_step(c, k & 1, c->timing ? k : -1);
+  } catch (...) {
+    cudaStreamEndCapture(c->s, &g);
+    throw;
+  }
+  ck(cudaStreamEndCapture(c->s, &g), "end capture");
+  cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  ck(e, "graph instantiate");
+  c->graph_dirty = false;
+}
+
+void accumulate_timing(tsbts_ctx* c, int real_steps) {
+  for (int k = 0; k < real_steps; ++k) {
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]),
+       "event elapsed");
+    c->force_ms += ms;
+    c->force_launches += 1;
+  }
+}
+
+struct NoProgress {};
+
+// Every block step advances the block time by at least one tick, so a pass
+// has at most (tau_e - t_sys) steps; a chunk without any step that did not
+// end the pass means the step loop is broken.
+void check_progress(tsbts_ctx* c, int real, long long pass_steps,
+                    long long tau_e) {
+  if (real <= 0 || pass_steps > tau_e - c->t_sys) throw NoProgress{};
+}
+
+// run one pass; returns the device error bits
+int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
+  History& cur = (pass & 1) ? c->H[1] : c->H[0];
+  launch_pass_begin(c->d_ctl, c->t_sys, tau_e, pass, (int)c->eras, c->n, c->s);
+  launch_pass_setup(c->B, c->P, cur, c->s);
+  ck(cudaGetLastError(), "pass set-up");
+  c->launches += 2;
+  const int G = c->cfg.graph_steps;
+  unsigned long long steps0 = c->h_ctl->steps;
+  long long pass_steps = 0;
+  if (G > 0) {
+    if (c->graph_dirty || !c->gexec) build_graph(c);
+    for (;;) {
+      ck(cudaGraphLaunch(c->gexec, c->s), "graph launch");
+      c->launches += 3LL * G;
+      read_ctl(c);
+      const int real = (int)(c->h_ctl->steps - steps0);
+      steps0 = c->h_ctl->steps;
+      if (c->timing) accumulate_timing(c, real);
+      if (c->h_ctl->done || c->h_ctl->err) break;
+      check_progress(c, real, pass_steps += real, tau_e);
+    }
+  } else {
+    long long chunk = std::max<long long>(4, std::min<long long>(
+                                                  est_steps / 2 + 1, 256));
+    int p = 0;
+    for (;;) {
+      if (c->timing) ensure_events(c, (int)chunk);
+      for (long long k = 0; k < chunk; ++k) {
+        enqueue_step(c, p, c->timing ? (int)k : -1);
+        c->launches += 3;
+        p ^= 1;
+      }
+      read_ctl(c);
+      const int real = (int)(c->h_ctl->steps - steps0);
+      steps0 = c->h_ctl->steps;
+      if (c->timing) accumulate_timing(c, real);
+      if (c->h_ctl->done || c->h_ctl->err) break;
+      check_progress(c, real, pass_steps += real, tau_e);
+      chunk = std::min<long long>(chunk * 2, 256);
+    }
+  }
+  c->passes += 1;
+  const long long nrec = std::max(c->h_ctl->slot[0].nrec, c->h_ctl->slot[1].nrec);
+  c->max_rec = std::max(c->max_rec, nrec);
+  return c->h_ctl->err;
+}
+
+long long era_ticks(tsbts_ctx* c) {
+  if (c->cfg.era_mode == 0) return 1LL << (c->cfg.k_max - c->cfg.era_log2);
+  // Alg. 3: last block time - first block time, clamped, power of two
+  const long long lo0 = LLONG_MAX, hi0 = LLONG_MIN;
+  ck(cudaMemcpyAsync(&c->d_ctl->first, &lo0, sizeof lo0,
+                     cudaMemcpyHostToDevice, c->s), "era reset");
+  ck(cudaMemcpyAsync(&c->d_ctl->last, &hi0, sizeof hi0,
+                     cudaMemcpyHostToDevice, c->s), "era reset");
+  launch_next_time_extrema(c->B, c->d_ctl, c->s);
+  c->launches += 1;
+  read_ctl(c);
+  long long lo = c->dtmax_t >> c->cfg.dyn_min_log2;
+  if (lo < 1) lo = 1;
+  long long e = c->h_ctl->last - c->h_ctl->first;
+  e = std::min(std::max(e, lo), c->dtmax_t);
+  long long p2 = 1;
+  while (2 * p2 <= e) p2 *= 2;
+  return p2;
+}
+
+int step_era_impl(tsbts_ctx* c, long long tau_end) {
+  while (c->t_sys < tau_end) {
+    const long long tau_e = std::min(c->t_sys + era_ticks(c), tau_end);
+    launch_copy_state(c->snap, c->B, c->s);
+    c->launches += 1;
+    for (;;) {
+      bool grow = false;
+      long long est = 0;
+      for (int p = 0; p < c->cfg.n_iter; ++p) {
+        if (p > 0) {
+          launch_copy_state(c->B, c->snap, c->s);
+          c->launches += 1;
+        }
+        const unsigned long long s0 = c->h_ctl->steps;
+        const int e = run_pass(c, p, tau_e, est);
+        est = (long long)(c->h_ctl->steps - s0);
+        if (e & kErrHistory) {
+          grow = true;
+          break;
+        }
+        if (e & kErrNonFinite)
+          return fail(c, TSBTS_ERR_NONFINITE,
+                      "non-finite force or step estimate (era " +
+                          std::to_string(c->eras) + ")");
+        if (e)
+          return fail(c, TSBTS_ERR_CUDA,
+                      "internal block-step invariant broken (bits " +
+                          std::to_string(e) + ")");
+      }
+      if (!grow) break;
+      // the history did not fit: grow both buffers, re-run the era
+      const long long cap = std::max(c->H[0].cap * 4, c->max_rec * 2);
+      ck(cudaStreamSynchronize(c->s), "synchronize");
+      alloc_history(c, 0, cap);
+      alloc_history(c, 1, cap);
+      int zero = 0;
+      ck(cudaMemcpyAsync(&c->d_ctl->err, &zero, sizeof zero,
+                         cudaMemcpyHostToDevice, c->s), "clear error");
+      launch_copy_state(c->B, c->snap, c->s);
+      c->launches += 1;
+      c->restarts += 1;
+    }
+    c->t_sys = tau_e;
+    c->eras += 1;
+  }
+  return TSBTS_OK;
+}
+
+void setup_bodies(tsbts_ctx* c, int n) {
+  Bodies& B = c->B;
+  B = Bodies{};
+  B.n = n;
+  auto& L = c->allocs;
+  B.m = dalloc<double>(L, n);
+  for (int d = 0; d < 3; ++d) {
+    B.r[d] = dalloc<double>(L, n);
+    B.v[d] = dalloc<double>(L, n);
+    B.a[d] = dalloc<double>(L, n);
+    B.pr[d] = dalloc<double>(L, n);
+    B.pv[d] = dalloc<double>(L, n);
+  }
+  B.dts = dalloc<double>(L, n);
+  B.tau = dalloc<long long>(L, n);
+  B.dt = dalloc<long long>(L, n);
+  B.jhi = dalloc<float4>(L, n);
+  B.jlo = dalloc<float4>(L, n);
+  B.jv = dalloc<float4>(L, n);
+  B.act = dalloc<int>(L, n);
+  B.cursor = dalloc<int>(L, n);
+  B.last = dalloc<int>(L, n);
+  B.part_cap = std::max<long long>(c->fl.part_cap, 5LL * n);
+  B.part = dalloc<double>(L, B.part_cap);
+  Bodies& S = c->snap;
+  S = Bodies{};
+  S.n = n;
+  for (int d = 0; d < 3; ++d) {
+    S.r[d] = dalloc<double>(L, n);
+    S.v[d] = dalloc<double>(L, n);
+    S.a[d] = dalloc<double>(L, n);
+  }
+  S.dts = dalloc<double>(L, n);
+  S.tau = dalloc<long long>(L, n);
+  S.dt = dalloc<long long>(L, n);
+  c->d_ctl = dalloc<Ctl>(L, 1);
+  c->d_w = dalloc<double>(L, n);
+  c->d_eout = dalloc<double>(L, 2);
+  c->d_nsplit = dalloc<int>(L, 1);
+  ck(cudaMallocHost(&c->h_ctl, sizeof(Ctl)), "cudaMallocHost");
+  std::memset(c->h_ctl, 0, sizeof(Ctl));
+  ck(cudaMemsetAsync(c->d_ctl, 0, sizeof(Ctl), c->s), "memset");
+  const long long cap = std::max<long long>(8LL * n, 1LL << 16);
+  alloc_history(c, 0, cap);
+  alloc_history(c, 1, cap);
+}
+
+int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
+                const double* v, double eps, double eta, double dt_max,
+                bool host) {
+  if (!c) return TSBTS_ERR_ARG;
+  if (c->poisoned) return fail(c, TSBTS_ERR_STATE, "context is poisoned");
+  if (n < 1 || n > (1LL << 24))
+    return fail(c, TSBTS_ERR_ARG, "n must be in [1, 2^24]");
+  if (!m || !r || !v) return fail(c, TSBTS_ERR_ARG, "null input pointer");
+  if (!(eps >= 0.0) || !std::isfinite(eps))
+    return fail(c, TSBTS_ERR_ARG, "eps must be finite and >= 0");
+  if (!(eta > 0.0) || !std::isfinite(eta))
+    return fail(c, TSBTS_ERR_ARG, "eta must be finite and > 0");
+  int k_min = 0;
+  if (!valid_dt_max(dt_max, c->cfg.k_max, &k_min))
+    return fail(c, TSBTS_ERR_ARG, "dt_max must be 2^-k with 0 <= k <= k_max");
+  if (c->cfg.era_mode == 0 && c->cfg.era_log2 > c->cfg.k_max)
+    return fail(c, TSBTS_ERR_ARG, "era_log2 must be <= k_max");
+  try {
+    ck(cudaSetDevice(c->cfg.device), "cudaSetDevice");
+    release_all(c);
+    c->n = (int)n;
+    c->eps = eps;
+    c->eta = eta;
+    c->k_min = k_min;
+    c->dtmax_t = 1LL << (c->cfg.k_max - k_min);
+    c->t_sys = 0;
+    c->eras = c->passes = c->restarts = c->max_rec = 0;
+    c->force_ms = 0;
+    c->force_launches = 0;
+    c->launches = 0;
+    c->exact = c->cfg.precision == TSBTS_FP64 &&
+               (c->cfg.exact_order == 1 ||
+                (c->cfg.exact_order < 0 && n <= 8192));
+    c->fl = force_launch_shape(c->cfg.precision, c->cfg.device);
+    c->correct_grid = std::max(1, std::min(c->sms * 8, (c->n + 127) / 128));
+    setup_bodies(c, (int)n);
+    Params& P = c->P;
+    P = Params{};
+    P.eps2 = eps * eps;
+    P.eta = eta;
+    P.inv_ticks = std::ldexp(1.0, -c->cfg.k_max);
+    P.dtmax_t = c->dtmax_t;
+    P.k_min = k_min;
+    P.k_max = c->cfg.k_max;
+    P.precision = c->cfg.precision;
+    P.exact = c->exact;
+    P.ctl = c->d_ctl;
+    P.lg_cap = 0;
+    // inputs to the device
+    const double *dm = m, *dr = r, *dv = v;
+    std::vector<void*> tmp;
+    if (host) {
+      double* t = dalloc<double>(tmp, 7 * (size_t)n);
+      ck(cudaMemcpyAsync(t, m, sizeof(double) * n, cudaMemcpyHostToDevice,
+                         c->s), "copy m");
+      ck(cudaMemcpyAsync(t + n, r, sizeof(double) * 3 * n,
+                         cudaMemcpyHostToDevice, c->s), "copy r");
+      ck(cudaMemcpyAsync(t + 4 * n, v, sizeof(double) * 3 * n,
+                         cudaMemcpyHostToDevice, c->s), "copy v");
+      dm = t;
+      dr = t + n;
+      dv = t + 4 * n;
+    }
+    launch_load_aos(c->B, dm, dr, dv, c->d_ctl, c->s);
+    // Alg. 2 step 1: forces on every body, first steps
+    launch_init_jdata(c->B, P, c->s);
+    ForceArgs fa = force_args_engine(c, 0);
+    fa.n_act_fixed = c->n;
+    fa.n_act_ptr = nullptr;
+    fa.nsplit_out = c->d_nsplit;
+    fa.done = nullptr;
+    ck(launch_force(c->cfg.precision, fa, c->fl, c->s), "init force");
+    launch_init_finalize(c->B, P, c->d_nsplit, c->s);
+    ck(cudaGetLastError(), "init kernels");
+    c->launches = 4;
+    read_ctl(c);
+    free_list(tmp);
+    if (c->h_ctl->err & kErrNonFinite)
+      return fail(c, TSBTS_ERR_NONFINITE, "non-finite input or initial force");
+    c->inited = true;
+    c->graph_dirty = true;
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(c, f);
+  } catch (const std::bad_alloc&) {
+    return fail(c, TSBTS_ERR_CUDA, "host out of memory");
+  }
+}
+
+int check_ready(tsbts_ctx* c) {
+  if (!c) return TSBTS_ERR_ARG;
+  if (c->poisoned) return fail(c, TSBTS_ERR_STATE, "context is poisoned");
+  if (!c->inited) return fail(c, TSBTS_ERR_STATE, "tsbts_init not called");
+  return TSBTS_OK;
+}
+
+// ---------------------------------------------------------------------
+// scratch of the stand-alone force entry point, per device
+// ---------------------------------------------------------------------
+struct Scratch {
+  int n_cap = 0;
+  long long part_cap = 0;
+  double* soa = nullptr;  // 7 n doubles (x, y, z, vx, vy, vz, m)
+  float4* j4 = nullptr;   // 3 n float4
+  double* part = nullptr;
+  int* nsplit = nullptr;
+};
+std::mutex g_scratch_mu;
+std::vector<Scratch> g_scratch;
+
+}  // namespace
+
+extern "C" {
+
+void tsbts_config_default(tsbts_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->precision = TSBTS_FP64;
+  cfg->n_iter = 3;
+  cfg->era_mode = 0;
+  cfg->era_log2 = 3;
+  cfg->dyn_min_log2 = 3;
+  cfg->k_max = 20;
+  cfg->exact_order = -1;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->graph_steps = 32;
+}
+
+int tsbts_create(tsbts_ctx** out, const tsbts_config* cfg) {
+  if (!out || !cfg) return TSBTS_ERR_ARG;
+  *out = nullptr;
+  if (cfg->precision != TSBTS_FP64 && cfg->precision != TSBTS_MIXED)
+    return TSBTS_ERR_ARG;
+  if (cfg->n_iter < 1 || cfg->n_iter > 64) return TSBTS_ERR_ARG;
+  if (cfg->era_mode != 0 && cfg->era_mode != 1) return TSBTS_ERR_ARG;
+  if (cfg->k_max < 1 || cfg->k_max > 40) return TSBTS_ERR_ARG;
+  if (cfg->era_log2 < 0 || cfg->era_log2 > cfg->k_max) return TSBTS_ERR_ARG;
+  if (cfg->dyn_min_log2 < 0 || cfg->dyn_min_log2 > 40) return TSBTS_ERR_ARG;
+  if (cfg->graph_steps < 0 || cfg->graph_steps > 4096 ||
+      (cfg->graph_steps & 1))
+    return TSBTS_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 ||
+      cfg->device >= ndev) {
+    cudaGetLastError();
+    return TSBTS_ERR_CUDA;
+  }
+  tsbts_ctx* c = new (std::nothrow) tsbts_ctx;
+  if (!c) return TSBTS_ERR_CUDA;
+  c->cfg = *cfg;
+  try {
+    ck(cudaSetDevice(cfg->device), "cudaSetDevice");
+    ck(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount,
+                              cfg->device), "device attribute");
+    if (cfg->stream) {
+      c->s = (cudaStream_t)cfg->stream;
+    } else {
+      ck(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking),
+         "cudaStreamCreate");
+      c->own_stream = true;
+    }
+  } catch (const CudaFail&) {
+    delete c;
+    return TSBTS_ERR_CUDA;
+  }
+  *out = c;
+  return TSBTS_OK;
+}
+
+int tsbts_init(tsbts_ctx* ctx, int64_t n, const double* m, const double* r,
+               const double* v, double eps, double eta, double dt_max) {
+  if (ctx && m && r && v && n > 0 && n <= (1LL << 24)) {
+    for (int64_t i = 0; i < n; ++i) {
+      bool ok = std::isfinite(m[i]);
+      for (int d = 0; d < 3; ++d)
+        ok = ok && std::isfinite(r[3 * i + d]) && std::isfinite(v[3 * i + d]);
+      if (!ok)
+        return fail(ctx, TSBTS_ERR_NONFINITE,
+                    "non-finite input at body " + std::to_string(i));
+    }
+  }
+  return init_common(ctx, n, m, r, v, eps, eta, dt_max, true);
+}
+
+int tsbts_init_device(tsbts_ctx* ctx, int64_t n, const double* m_dev,
+                      const double* r_dev, const double* v_dev, double eps,
+                      double eta, double dt_max) {
+  return init_common(ctx, n, m_dev, r_dev, v_dev, eps, eta, dt_max, false);
+}
+
+int tsbts_step_era(tsbts_ctx* ctx, double t_end, double* t_reached) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  const double te = std::ldexp(t_end, ctx->cfg.k_max);
+  if (!std::isfinite(te) || te != std::floor(te) || te > 9.0e18 ||
+      (long long)te < ctx->t_sys)
+    return fail(ctx, TSBTS_ERR_ARG,
+                "t_end must be a whole number of ticks, not in the past");
+  try {
+    ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+    rc = step_era_impl(ctx, (long long)te);
+    if (t_reached) *t_reached = std::ldexp((double)ctx->t_sys, -ctx->cfg.k_max);
+    return rc;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  } catch (const NoProgress&) {
+    return fail(ctx, TSBTS_ERR_TIMEOUT, "block-step loop made no progress");
+  } catch (const std::bad_alloc&) {
+    return fail(ctx, TSBTS_ERR_HISTORY, "host out of memory");
+  }
+}
+
+int tsbts_energy(tsbts_ctx* ctx, double* ekin, double* epot, double* etot) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  try {
+    ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+    launch_energy(ctx->B, ctx->P, ctx->t_sys, ctx->d_w, ctx->d_eout, ctx->sms,
+                  ctx->s);
+    ck(cudaGetLastError(), "energy kernels");
+    ctx->launches += 3;
+    double e[2];
+    ck(cudaMemcpyAsync(e, ctx->d_eout, sizeof e, cudaMemcpyDeviceToHost,
+                       ctx->s), "read energy");
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    if (ekin) *ekin = e[0];
+    if (epot) *epot = e[1];
+    if (etot) *etot = e[0] + e[1];
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
+int tsbts_state(tsbts_ctx* ctx, double* t, double* m, double* r, double* v,
+                double* a, int64_t* tau_ticks, int64_t* dt_ticks) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  try {
+    ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+    const int n = ctx->n;
+    std::vector<double> buf(3 * (size_t)n);
+    auto vec = [&](double* dst, double* const src[3]) {
+      if (!dst) return;
+      for (int d = 0; d < 3; ++d)
+        ck(cudaMemcpyAsync(buf.data() + (size_t)d * n, src[d],
+                           sizeof(double) * n, cudaMemcpyDeviceToHost,
+                           ctx->s), "read state");
+      ck(cudaStreamSynchronize(ctx->s), "synchronize");
+      for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d)
+          dst[3 * (size_t)i + d] = buf[(size_t)d * n + i];
+    };
+    if (t) *t = std::ldexp((double)ctx->t_sys, -ctx->cfg.k_max);
+    if (m)
+      ck(cudaMemcpyAsync(m, ctx->B.m, sizeof(double) * n,
+                         cudaMemcpyDeviceToHost, ctx->s), "read m");
+    if (tau_ticks)
+      ck(cudaMemcpyAsync(tau_ticks, ctx->B.tau, sizeof(int64_t) * n,
+                         cudaMemcpyDeviceToHost, ctx->s), "read tau");
+    if (dt_ticks)
+      ck(cudaMemcpyAsync(dt_ticks, ctx->B.dt, sizeof(int64_t) * n,
+                         cudaMemcpyDeviceToHost, ctx->s), "read dt");
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    vec(r, ctx->B.r);
+    vec(v, ctx->B.v);
+    vec(a, ctx->B.a);
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
+int tsbts_get_stats(tsbts_ctx* ctx, tsbts_stats* out) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (!out) return fail(ctx, TSBTS_ERR_ARG, "null stats pointer");
+  try {
+    read_ctl(ctx);
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+  std::memset(out, 0, sizeof *out);
+  out->block_steps = (int64_t)ctx->h_ctl->steps;
+  out->interactions = (int64_t)ctx->h_ctl->inter;
+  out->eras = ctx->eras;
+  out->passes = ctx->passes;
+  out->dt_underflow = (int64_t)ctx->h_ctl->underflow;
+  out->era_restarts = ctx->restarts;
+  out->history_capacity = ctx->H[0].cap;
+  out->t_sys_ticks = ctx->t_sys;
+  out->force_ms = ctx->force_ms;
+  out->force_launches = ctx->force_launches;
+  out->kernel_launches = ctx->launches;
+  return TSBTS_OK;
+}
+
+int tsbts_set_timing(tsbts_ctx* ctx, int enable) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (ctx->timing != (enable != 0)) {
+    ctx->timing = enable != 0;
+    ctx->graph_dirty = true;
+  }
+  return TSBTS_OK;
+}
+
+int tsbts_schedule_log(tsbts_ctx* ctx, int64_t capacity_entries) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (capacity_entries < 0)
+    return fail(ctx, TSBTS_ERR_ARG, "capacity must be >= 0");
+  try {
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    free_list(ctx->lg_allocs);
+    Params& P = ctx->P;
+    P.lg_cap = capacity_entries;
+    P.lg_era = P.lg_pass = P.lg_nact = P.lg_i = nullptr;
+    P.lg_tau = P.lg_dt = nullptr;
+    if (capacity_entries > 0) {
+      auto& L = ctx->lg_allocs;
+      P.lg_era = dalloc<int>(L, capacity_entries);
+      P.lg_pass = dalloc<int>(L, capacity_entries);
+      P.lg_nact = dalloc<int>(L, capacity_entries);
+      P.lg_tau = dalloc<long long>(L, capacity_entries);
+      P.lg_i = dalloc<int>(L, capacity_entries);
+      P.lg_dt = dalloc<long long>(L, capacity_entries);
+    }
+    const long long zero[3] = {0, 0, 0};
+    ck(cudaMemcpyAsync(&ctx->d_ctl->log_steps, zero, sizeof zero,
+                       cudaMemcpyHostToDevice, ctx->s), "reset log");
+    ctx->graph_dirty = true;
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
+int tsbts_schedule_size(tsbts_ctx* ctx, int64_t* steps, int64_t* entries,
+                        int64_t* dropped) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  try {
+    read_ctl(ctx);
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+  const long long cap = ctx->P.lg_cap;
+  if (steps) *steps = std::min<long long>(ctx->h_ctl->log_steps, cap);
+  if (entries) *entries = std::min<long long>(ctx->h_ctl->log_ent, cap);
+  if (dropped)
+    *dropped = ctx->h_ctl->log_drop +
+               std::max<long long>(0, ctx->h_ctl->log_steps - cap);
+  return TSBTS_OK;
+}
+
+int tsbts_schedule_get(tsbts_ctx* ctx, int32_t* step_era, int32_t* step_pass,
+                       int64_t* step_tau, int32_t* step_nact, int32_t* ent_i,
+                       int64_t* ent_dt) {
+  int64_t ns = 0, ne = 0, dr = 0;
+  int rc = tsbts_schedule_size(ctx, &ns, &ne, &dr);
+  if (rc) return rc;
+  try {
+    const Params& P = ctx->P;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+      if (dst && bytes)
+        ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->s),
+           "read log");
+    };
+    cp(step_era, P.lg_era, sizeof(int32_t) * ns);
+    cp(step_pass, P.lg_pass, sizeof(int32_t) * ns);
+    cp(step_tau, P.lg_tau, sizeof(int64_t) * ns);
+    cp(step_nact, P.lg_nact, sizeof(int32_t) * ns);
+    cp(ent_i, P.lg_i, sizeof(int32_t) * ne);
+    cp(ent_dt, P.lg_dt, sizeof(int64_t) * ne);
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
+const char* tsbts_last_error(const tsbts_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+void tsbts_destroy(tsbts_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->cfg.device);
+  release_all(ctx);
+  if (ctx->own_stream && ctx->s) cudaStreamDestroy(ctx->s);
+  cudaGetLastError();
+  delete ctx;
+}
+
+int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
+                const double* r, const double* v, double eps, int64_t n_act,
+                const int32_t* idx, double* a, double* phi, double* q,
+                void* stream) {
+  if (precision != TSBTS_FP64 && precision != TSBTS_MIXED) return TSBTS_ERR_ARG;
+  if (n < 1 || n > 0x7fffffffLL || n_act < 0 || n_act > 0x7fffffffLL)
+    return TSBTS_ERR_ARG;
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return TSBTS_ERR_ARG;
+  if (!m || !r || !v || (n_act > 0 && (!idx || !a || !phi || !q)))
+    return TSBTS_ERR_ARG;
+  if (n_act == 0) return TSBTS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "cudaGetDevice");
+    const ForceLaunch fl = force_launch_shape(precision, dev);
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if ((int)g_scratch.size() <= dev) g_scratch.resize(dev + 1);
+    Scratch& S = g_scratch[dev];
+    const long long need_part = std::max<long long>(fl.part_cap, 5LL * n_act);
+    if (S.n_cap < n || S.part_cap < need_part) {
+      ck(cudaDeviceSynchronize(), "synchronize before scratch growth");
+      cudaFree(S.soa);
+      cudaFree(S.j4);
+      cudaFree(S.part);
+      cudaFree(S.nsplit);
+      S = Scratch{};
+      const int ncap = (int)std::max<int64_t>(n, S.n_cap);
+      ck(cudaMalloc(&S.soa, sizeof(double) * 7 * (size_t)ncap), "scratch");
+      ck(cudaMalloc(&S.j4, sizeof(float4) * 3 * (size_t)ncap), "scratch");
+      ck(cudaMalloc(&S.part, sizeof(double) * need_part), "scratch");
+      ck(cudaMalloc(&S.nsplit, sizeof(int)), "scratch");
+      S.n_cap = ncap;
+      S.part_cap = need_part;
+    }
+    const int ni = (int)n;
+    double* x = S.soa;
+    float4* j4 = S.j4;
+    ck(launch_pack_aos(precision, ni, m, r, v, x, x + ni, x + 2LL * ni,
+                       x + 3LL * ni, x + 4LL * ni, x + 5LL * ni, x + 6LL * ni,
+                       j4, j4 + ni, j4 + 2LL * ni, s),
+       "pack");
+    ForceArgs fa{};
+    fa.n = ni;
+    fa.m = x + 6LL * ni;
+    for (int d = 0; d < 3; ++d) {
+      fa.x[d] = x + (long long)d * ni;
+      fa.w[d] = x + (long long)(3 + d) * ni;
+    }
+    fa.jhi = j4;
+    fa.jlo = j4 + ni;
+    fa.jv = j4 + 2LL * ni;
+    fa.idx = idx;
+    fa.n_act_fixed = (int)n_act;
+    fa.nsplit_out = S.nsplit;
+    fa.part = S.part;
+    fa.part_cap = S.part_cap;
+    fa.eps2 = eps * eps;
+    fa.eps2f = (float)(eps * eps);
+    fa.exact = precision == TSBTS_FP64 &&
+               (exact_order == 1 || (exact_order < 0 && n <= 8192));
+    ck(launch_force(precision, fa, fl, s), "force");
+    ck(launch_force_finalize(S.part, S.nsplit, (int)n_act, a, phi, q, s),
+       "force finalize");
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    std::fprintf(stderr, "tsbts_force: %s: %s\n", f.what,
+                 cudaGetErrorString(f.e));
+    return TSBTS_ERR_CUDA;
+  }
+}
+
+int tsbts_release_scratch(void) {
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TSBTS_ERR_CUDA;
+  if ((int)g_scratch.size() <= dev) return TSBTS_OK;
+  Scratch& S = g_scratch[dev];
+  cudaDeviceSynchronize();
+  cudaFree(S.soa);
+  cudaFree(S.j4);
+  cudaFree(S.part);
+  cudaFree(S.nsplit);
+  S = Scratch{};
+  return TSBTS_OK;
+}
+
+const char* tsbts_version(void) { return kVersion; }
+
+}  // extern "C"

@@ -1,0 +1,537 @@
+// Block-step kernels of the TSBTS library (Sec. 2 Alg. 2 steps 3-8, Sec. 4
+// Alg. 3): era/pass set-up, block selection fused with the prediction or
+// time-symmetric interpolation of every body, correction (Eq. 1) with the
+// next-step choice (Eq. 4, Alg. 1) and the era-history append, energy.
+//
+// The loop is device-resident: every kernel reads the block time, active
+// count and pass state from the control block, so a whole chunk of block
+// steps is launched (or replayed from a CUDA graph) without a host round
+// trip; once the block time passes the era end every kernel returns.
+//
+// Block selection uses the commensurability of block steps: each body sits
+// on a multiple of its own power-of-two step, so the next block time is the
+// next multiple of the smallest populated step after the current block
+// time, and a per-level body count (updated by the correction kernel)
+// replaces the paper's sort by block time.
+#include "tsbts_kernels.cuh"
+
+namespace tsbts {
+
+// ---------------------------------------------------------------------
+// Pass set-up
+// ---------------------------------------------------------------------
+__global__ void pass_begin_kernel(Ctl* ctl, long long tau_s, long long tau_e,
+                                  int pass, int era, int n) {
+  if (threadIdx.x < kMaxLevels) ctl->hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    const long long lg = ctl->log_ent;
+    for (int p = 0; p < 2; ++p) {
+      ctl->slot[p].tau_c = tau_s;
+      ctl->slot[p].tau_next = 0;
+      ctl->slot[p].nrec = n;
+      ctl->slot[p].lg_base = lg;
+      ctl->slot[p].cnt = 0;
+      ctl->slot[p].nsplit = 0;
+    }
+    ctl->tau_e = tau_e;
+    ctl->done = 0;
+    ctl->pass = pass;
+    ctl->era = era;
+  }
+}
+
+// era-start record of every body, cursors, and the level histogram
+__global__ void pass_setup_kernel(Bodies B, Params P, History cur) {
+  __shared__ int h[kMaxLevels];
+  for (int t = threadIdx.x; t < kMaxLevels; t += blockDim.x) h[t] = 0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n;
+       i += gridDim.x * blockDim.x) {
+    cur.tau[i] = B.tau[i];
+    for (int c = 0; c < 3; ++c) {
+      cur.r[c][i] = B.r[c][i];
+      cur.v[c][i] = B.v[c][i];
+      cur.a[c][i] = B.a[c][i];
+    }
+    cur.dts[i] = B.dts[i];
+    cur.next[i] = -1;
+    B.last[i] = i;
+    B.cursor[i] = i;
+    atomicAdd(&h[level_of(B.dt[i], P.k_max)], 1);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kMaxLevels; t += blockDim.x)
+    if (h[t]) atomicAdd(&P.ctl->hist[t], h[t]);
+}
+
+// ---------------------------------------------------------------------
+// Step A: block time, active list, prediction of every body (Alg. 2
+// steps 3-4; Eq. 2; time-symmetric interpolation in passes >= 1).
+// ---------------------------------------------------------------------
+__device__ __forceinline__ void store_prediction(const Bodies& B,
+                                                 const Params& P, int j,
+                                                 const double rp[3],
+                                                 const double vp[3]) {
+  if (P.precision == 0) {
+    for (int c = 0; c < 3; ++c) {
+      B.pr[c][j] = rp[c];
+      B.pv[c][j] = vp[c];
+    }
+  } else {
+    const float xh = (float)rp[0], yh = (float)rp[1], zh = (float)rp[2];
+    B.jhi[j] = make_float4(xh, yh, zh, (float)B.m[j]);
+    B.jlo[j] = make_float4((float)(rp[0] - (double)xh),
+                           (float)(rp[1] - (double)yh),
+                           (float)(rp[2] - (double)zh), 0.f);
+    B.jv[j] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
+  }
+}
+
+__global__ void select_predict_kernel(Bodies B, Params P, History HA,
+                                      History HB, int p) {
+  __shared__ long long s_tn;
+  __shared__ int s_stop;
+  Ctl* ctl = P.ctl;
+  if (threadIdx.x == 0) {
+    int stop = ctl->done ? 3 : 0;
+    long long tn = 0;
+    if (!stop) {
+      int kk = -1;
+      for (int k = P.k_max; k >= 0; --k)
+        if (ctl->hist[k] > 0) {
+          kk = k;
+          break;
+        }
+      if (kk < 0) {
+        stop = 1;
+      } else {
+        const long long D = 1LL << (P.k_max - kk);
+        tn = (ctl->slot[p].tau_c / D + 1) * D;
+        if (tn > ctl->tau_e) stop = 2;
+      }
+    }
+    s_tn = tn;
+    s_stop = stop;
+  }
+  __syncthreads();
+  if (s_stop) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && s_stop != 3) {
+      if (s_stop == 1) atomicOr(&ctl->err, kErrLevels);
+      ctl->done = 1;
+    }
+    return;
+  }
+  const long long tn = s_tn;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->slot[p].tau_next = tn;
+  const int pass = ctl->pass;
+  const History& prev = (pass & 1) ? HA : HB;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = false;
+  if (j < B.n) {
+    const long long tj = B.tau[j];
+    const long long nt = tj + B.dt[j];
+    act = (nt == tn);
+    if (nt < tn) atomicOr(&ctl->err, kErrInvariant);
+    double rp[3], vp[3];
+    bool have = false;
+    if (pass > 0 && !act) {
+      int c = B.cursor[j];
+      if (prev.tau[c] <= tn) {
+        for (;;) {
+          const int nx = prev.next[c];
+          if (nx < 0 || prev.tau[nx] > tn) break;
+          c = nx;
+        }
+        B.cursor[j] = c;
+        if (prev.tau[c] == tn) {
+          for (int d = 0; d < 3; ++d) {
+            rp[d] = prev.r[d][c];
+            vp[d] = prev.v[d][c];
+          }
+          have = true;
+        } else {
+          const int nx = prev.next[c];
+          if (nx >= 0) {
+            const HermiteW w =
+                hermite_weights(prev.tau[c], prev.tau[nx], tn, P.inv_ticks);
+            for (int d = 0; d < 3; ++d) {
+              rp[d] = hermite1(w, prev.r[d][c], prev.v[d][c], prev.r[d][nx],
+                               prev.v[d][nx]);
+              vp[d] = hermite1(w, prev.v[d][c], prev.a[d][c], prev.v[d][nx],
+                               prev.a[d][nx]);
+            }
+            have = true;
+          }
+        }
+      }
+    }
+    if (!have) {
+      const double h = __dmul_rn((double)(tn - tj), P.inv_ticks);
+      for (int d = 0; d < 3; ++d)
+        taylor1(B.r[d][j], B.v[d][j], B.a[d][j], h, rp[d], vp[d]);
+    }
+    store_prediction(B, P, j, rp, vp);
+  }
+  // compaction of the active list (order within a step is arbitrary)
+  const unsigned bal = __ballot_sync(kFull, act);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0 && bal) base = atomicAdd(&ctl->slot[p].cnt, __popc(bal));
+  base = __shfl_sync(kFull, base, 0);
+  if (act) B.act[base + __popc(bal & ((1u << lane) - 1u))] = j;
+}
+
+// ---------------------------------------------------------------------
+// Step C: correction (Eq. 1), next step (pass 0: standard block step;
+// passes >= 1: Alg. 1 with Eq. 4), history append, level counts.
+// ---------------------------------------------------------------------
+__global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
+                               int p) {
+  Ctl* ctl = P.ctl;
+  if (ctl->done) return;
+  const StepSlot sl = ctl->slot[p];
+  const int n_act = sl.cnt;
+  const long long tn = sl.tau_next;
+  const int S = sl.nsplit;
+  const int pass = ctl->pass;
+  const History& cur = (pass & 1) ? HB : HA;
+  const History& prev = (pass & 1) ? HA : HB;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act;
+       k += gridDim.x * blockDim.x) {
+    const int i = B.act[k];
+    double an[3], q;
+    {
+      const double* pp = B.part;
+      an[0] = pp[0 * n_act + k];
+      an[1] = pp[1 * n_act + k];
+      an[2] = pp[2 * n_act + k];
+      q = pp[4 * n_act + k];
+      for (int sp = 1; sp < S; ++sp) {
+        pp = B.part + (long long)sp * 5 * n_act;
+        an[0] = __dadd_rn(an[0], pp[0 * n_act + k]);
+        an[1] = __dadd_rn(an[1], pp[1 * n_act + k]);
+        an[2] = __dadd_rn(an[2], pp[2 * n_act + k]);
+        q = fmax(q, pp[4 * n_act + k]);
+      }
+    }
+    if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]) ||
+        !(q >= 0.0) || isnan(q))
+      atomicOr(&ctl->err, kErrNonFinite);
+    const long long d = B.dt[i];
+    const double h = __dmul_rn((double)d, P.inv_ticks);
+    double rn[3], vn[3];
+    for (int c = 0; c < 3; ++c) {
+      double rp, vp;
+      taylor1(B.r[c][i], B.v[c][i], B.a[c][i], h, rp, vp);
+      rn[c] = rp;
+      vn[c] = __dadd_rn(B.v[c][i],
+                        __dmul_rn(__dmul_rn(0.5, __dadd_rn(B.a[c][i], an[c])),
+                                  h));
+      B.r[c][i] = rn[c];
+      B.v[c][i] = vn[c];
+      B.a[c][i] = an[c];
+    }
+    B.tau[i] = tn;
+    const double dts = __ddiv_rn(P.eta, __dsqrt_rn(q));
+    B.dts[i] = dts;
+    const long long rec = sl.nrec + k;
+    if (rec < cur.cap) {
+      cur.tau[rec] = tn;
+      for (int c = 0; c < 3; ++c) {
+        cur.r[c][rec] = rn[c];
+        cur.v[c][rec] = vn[c];
+        cur.a[c][rec] = an[c];
+      }
+      cur.dts[rec] = dts;
+      cur.next[rec] = -1;
+      cur.next[B.last[i]] = (int)rec;
+      B.last[i] = (int)rec;
+    } else {
+      atomicOr(&ctl->err, kErrHistory);
+    }
+    int uf = 0;
+    long long c;
+    if (pass == 0) {
+      c = forward_step(tn, d, dts, P.k_min, P.k_max, &uf);
+    } else {
+      const int start = B.cursor[i];
+      const double e2 = history_dts_at(prev, start, tn + 2 * d, dts);
+      const double e1 = history_dts_at(prev, start, tn + d, dts);
+      c = symmetric_step(tn, d, dts, e2, e1, P.k_min, P.k_max, P.dtmax_t,
+                         &uf);
+    }
+    if (uf) atomicAdd(&ctl->underflow, 1ULL);
+    if (c != d) {
+      atomicSub(&ctl->hist[level_of(d, P.k_max)], 1);
+      atomicAdd(&ctl->hist[level_of(c, P.k_max)], 1);
+    }
+    B.dt[i] = c;
+    if (P.lg_cap > 0) {
+      const long long e = sl.lg_base + k;
+      if (e < P.lg_cap) {
+        P.lg_i[e] = i;
+        P.lg_dt[e] = c;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    StepSlot& nx = ctl->slot[p ^ 1];
+    nx.tau_c = tn;
+    nx.tau_next = 0;
+    nx.nrec = sl.nrec + n_act;
+    nx.lg_base = sl.lg_base + n_act;
+    nx.cnt = 0;
+    nx.nsplit = 0;
+    ctl->steps += 1ULL;
+    ctl->inter += (unsigned long long)n_act * (unsigned long long)B.n;
+    if (P.lg_cap > 0) {
+      const long long s = ctl->log_steps;
+      if (s < P.lg_cap) {
+        P.lg_era[s] = ctl->era;
+        P.lg_pass[s] = pass;
+        P.lg_tau[s] = tn;
+        P.lg_nact[s] = n_act;
+      }
+      ctl->log_steps = s + 1;
+      const long long over = sl.lg_base + n_act - P.lg_cap;
+      ctl->log_drop += over <= 0 ? 0 : (over < n_act ? over : n_act);
+      ctl->log_ent = sl.lg_base + n_act;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// Era helpers: snapshot/restore, next-time extrema (Alg. 3)
+// ---------------------------------------------------------------------
+__global__ void copy_state_kernel(Bodies dst, Bodies src) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dst.n;
+       i += gridDim.x * blockDim.x) {
+    for (int c = 0; c < 3; ++c) {
+      dst.r[c][i] = src.r[c][i];
+      dst.v[c][i] = src.v[c][i];
+      dst.a[c][i] = src.a[c][i];
+    }
+    dst.dts[i] = src.dts[i];
+    dst.tau[i] = src.tau[i];
+    dst.dt[i] = src.dt[i];
+  }
+}
+
+__global__ void next_time_extrema_kernel(Bodies B, Ctl* ctl) {
+  long long lo = LLONG_MAX, hi = LLONG_MIN;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n;
+       i += gridDim.x * blockDim.x) {
+    const long long t = B.tau[i] + B.dt[i];
+    lo = t < lo ? t : lo;
+    hi = t > hi ? t : hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long a = __shfl_xor_sync(kFull, lo, o);
+    const long long b = __shfl_xor_sync(kFull, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&ctl->first, lo);
+    atomicMax(&ctl->last, hi);
+  }
+}
+
+// ---------------------------------------------------------------------
+// Initialisation (Alg. 2 step 1)
+// ---------------------------------------------------------------------
+__global__ void load_aos_kernel(Bodies B, const double* m, const double* r,
+                                const double* v, Ctl* ctl) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n;
+       i += gridDim.x * blockDim.x) {
+    B.m[i] = m[i];
+    bool ok = isfinite(m[i]);
+    for (int c = 0; c < 3; ++c) {
+      const double x = r[3LL * i + c], u = v[3LL * i + c];
+      B.r[c][i] = x;
+      B.v[c][i] = u;
+      B.a[c][i] = 0.0;
+      ok = ok && isfinite(x) && isfinite(u);
+    }
+    B.tau[i] = 0;
+    B.dt[i] = 1;
+    B.dts[i] = 0.0;
+    B.act[i] = i;
+    if (!ok) atomicOr(&ctl->err, kErrNonFinite);
+  }
+}
+
+// j data of the initial state (prediction to t = 0 is the state itself)
+__global__ void init_jdata_kernel(Bodies B, Params P) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B.n;
+       j += gridDim.x * blockDim.x) {
+    double rp[3], vp[3];
+    for (int c = 0; c < 3; ++c) {
+      rp[c] = B.r[c][j];
+      vp[c] = B.v[c][j];
+    }
+    store_prediction(B, P, j, rp, vp);
+  }
+}
+
+__global__ void init_finalize_kernel(Bodies B, Params P, const int* nsplit) {
+  const int S = *nsplit;
+  const int n = B.n;
+  Ctl* ctl = P.ctl;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
+    double an[3], q;
+    an[0] = B.part[0 * n + i];
+    an[1] = B.part[1 * n + i];
+    an[2] = B.part[2 * n + i];
+    q = B.part[4 * n + i];
+    for (int sp = 1; sp < S; ++sp) {
+      const double* pp = B.part + (long long)sp * 5 * n;
+      an[0] = __dadd_rn(an[0], pp[0 * n + i]);
+      an[1] = __dadd_rn(an[1], pp[1 * n + i]);
+      an[2] = __dadd_rn(an[2], pp[2 * n + i]);
+      q = fmax(q, pp[4 * n + i]);
+    }
+    if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]) || isnan(q))
+      atomicOr(&ctl->err, kErrNonFinite);
+    for (int c = 0; c < 3; ++c) B.a[c][i] = an[c];
+    const double dts = __ddiv_rn(P.eta, __dsqrt_rn(q));
+    B.dts[i] = dts;
+    int uf = 0;
+    B.dt[i] = level_ticks(dts, P.k_min, P.k_max, &uf);
+    if (uf) atomicAdd(&ctl->underflow, 1ULL);
+    B.tau[i] = 0;
+  }
+}
+
+// ---------------------------------------------------------------------
+// Energy at the system time (Sec. 3): Eq. 2 prediction of every body,
+// per-body pair sums over ascending j, body sums over ascending i.
+// ---------------------------------------------------------------------
+__global__ void energy_predict_kernel(Bodies B, Params P, long long T) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < B.n;
+       j += gridDim.x * blockDim.x) {
+    const double h = __dmul_rn((double)(T - B.tau[j]), P.inv_ticks);
+    for (int c = 0; c < 3; ++c) {
+      double rp, vp;
+      taylor1(B.r[c][j], B.v[c][j], B.a[c][j], h, rp, vp);
+      B.pr[c][j] = rp;
+      B.pv[c][j] = vp;
+    }
+  }
+}
+
+template <int NT, int TJ>
+__global__ void __launch_bounds__(NT) energy_pair_kernel(Bodies B, double eps2,
+                                                         double* w) {
+  __shared__ double sx[TJ], sy[TJ], sz[TJ], sm[TJ];
+  const int n = B.n;
+  for (int i0 = blockIdx.x * NT; i0 < n; i0 += gridDim.x * NT) {
+    const int i = i0 + threadIdx.x;
+    const bool valid = i < n;
+    const double xi = valid ? B.pr[0][i] : 0.0;
+    const double yi = valid ? B.pr[1][i] : 0.0;
+    const double zi = valid ? B.pr[2][i] : 0.0;
+    const double mi = valid ? B.m[i] : 0.0;
+    double wi = 0.0;
+    for (int jt = 0; jt < n; jt += TJ) {
+      const int cnt = min(TJ, n - jt);
+      __syncthreads();
+      for (int t = threadIdx.x; t < cnt; t += NT) {
+        sx[t] = B.pr[0][jt + t];
+        sy[t] = B.pr[1][jt + t];
+        sz[t] = B.pr[2][jt + t];
+        sm[t] = B.m[jt + t];
+      }
+      __syncthreads();
+      for (int t = 0; t < cnt; ++t) {
+        if (jt + t == i) continue;
+        const double dx = __dsub_rn(sx[t], xi);
+        const double dy = __dsub_rn(sy[t], yi);
+        const double dz = __dsub_rn(sz[t], zi);
+        const double s2 = __dadd_rn(
+            __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                      __dmul_rn(dz, dz)),
+            eps2);
+        wi = __dadd_rn(wi, __ddiv_rn(__dmul_rn(mi, sm[t]), __dsqrt_rn(s2)));
+      }
+    }
+    if (valid) w[i] = wi;
+  }
+}
+
+__global__ void energy_sum_kernel(Bodies B, const double* w, double* out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double k = 0.0, p = 0.0;
+  for (int i = 0; i < B.n; ++i) {
+    const double vx = B.pv[0][i], vy = B.pv[1][i], vz = B.pv[2][i];
+    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)),
+                                __dmul_rn(vz, vz));
+    k = __dadd_rn(k, __dmul_rn(__dmul_rn(0.5, B.m[i]), v2));
+    p = __dsub_rn(p, __dmul_rn(0.5, w[i]));
+  }
+  out[0] = k;
+  out[1] = p;
+}
+
+// ---------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------
+static inline int grid_for(int n, int threads, int cap = 1 << 16) {
+  int g = (n + threads - 1) / threads;
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+void launch_pass_begin(Ctl* ctl, long long tau_s, long long tau_e, int pass,
+                       int era, int n, cudaStream_t s) {
+  pass_begin_kernel<<<1, kMaxLevels, 0, s>>>(ctl, tau_s, tau_e, pass, era, n);
+}
+
+void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
+                       cudaStream_t s) {
+  pass_setup_kernel<<<grid_for(B.n, 256, 2048), 256, 0, s>>>(B, P, cur);
+}
+
+void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
+                           const History& HB, int p, cudaStream_t s) {
+  select_predict_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, P, HA, HB, p);
+}
+
+void launch_correct(const Bodies& B, const Params& P, const History& HA,
+                    const History& HB, int p, int grid, cudaStream_t s) {
+  correct_kernel<<<grid, 128, 0, s>>>(B, P, HA, HB, p);
+}
+
+void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s) {
+  copy_state_kernel<<<grid_for(dst.n, 256, 4096), 256, 0, s>>>(dst, src);
+}
+
+void launch_next_time_extrema(const Bodies& B, Ctl* ctl, cudaStream_t s) {
+  next_time_extrema_kernel<<<grid_for(B.n, 256, 1024), 256, 0, s>>>(B, ctl);
+}
+
+void launch_load_aos(const Bodies& B, const double* m, const double* r,
+                     const double* v, Ctl* ctl, cudaStream_t s) {
+  load_aos_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, m, r, v, ctl);
+}
+
+void launch_init_jdata(const Bodies& B, const Params& P, cudaStream_t s) {
+  init_jdata_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, P);
+}
+
+void launch_init_finalize(const Bodies& B, const Params& P, const int* nsplit,
+                          cudaStream_t s) {
+  init_finalize_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, P, nsplit);
+}
+
+void launch_energy(const Bodies& B, const Params& P, long long T, double* w,
+                   double* out, int sms, cudaStream_t s) {
+  energy_predict_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, P, T);
+  constexpr int NT = 128, TJ = 64;
+  int g = grid_for(B.n, NT);
+  energy_pair_kernel<NT, TJ><<<g, NT, 0, s>>>(B, P.eps2, w);
+  energy_sum_kernel<<<1, 32, 0, s>>>(B, w, out);
+  (void)sms;
+}
+
+}  // namespace tsbts

@@ -1,0 +1,273 @@
+// Internal declarations of the GB300 TSBTS library: device data layout,
+// control block of the device-resident block-step loop, and the FP64 step
+// arithmetic (Eq. 1, Eq. 2, Eq. 4, Alg. 1, time-symmetric interpolation).
+//
+// Every FP64 expression on the step path is written with explicit
+// round-to-nearest intrinsics (__dadd_rn, __dmul_rn, ...), which the
+// compiler never contracts into FMAs, in the order of the plain definition.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tsbts {
+
+constexpr int kMaxLevels = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+// device error bits (Ctl::err)
+constexpr int kErrHistory = 1;    // history buffer full: era must re-run
+constexpr int kErrNonFinite = 2;  // non-finite force, potential or q
+constexpr int kErrInvariant = 4;  // block-time invariant broken (bug)
+constexpr int kErrLevels = 8;     // level histogram empty (bug)
+
+// One pass's era history (Sec. 2: the state of every body at each of its
+// steps within the era). Records 0..n-1 are the era-start records of the
+// bodies; later records are appended in block-step order and chained per
+// body through `next` (-1 ends a chain).
+struct History {
+  long long* tau;
+  double* r[3];
+  double* v[3];
+  double* a[3];
+  double* dts;
+  int* next;
+  long long cap;
+};
+
+// Values of one block step. Two slots alternate between consecutive steps
+// so that no kernel reads a field that another block of the same kernel
+// writes.
+struct StepSlot {
+  long long tau_c;     // block time before this step
+  long long tau_next;  // this step's block time
+  long long nrec;      // records in the current history before this step
+  long long lg_base;   // schedule-log entries before this step
+  int cnt;             // active bodies (compaction counter)
+  int nsplit;          // j-split count chosen by the force kernel
+};
+
+struct Ctl {
+  StepSlot slot[2];
+  long long tau_e;          // era end (ticks)
+  long long first, last;    // next-time extrema for the dynamic era
+  unsigned long long steps;       // block steps taken (all passes)
+  unsigned long long inter;       // sum n_act * n
+  unsigned long long underflow;   // steps clamped to one tick
+  long long log_steps, log_ent, log_drop;
+  int done;     // pass finished: every kernel of the step loop returns
+  int pass;     // pass index within the era
+  int era;      // era index (schedule log)
+  int err;      // kErr* bits
+  int hist[kMaxLevels];  // bodies per level k (dt = 2^-k)
+};
+
+// Body arrays in HBM, structure of arrays, all length n.
+struct Bodies {
+  int n;
+  double* m;
+  double* r[3];
+  double* v[3];
+  double* a[3];
+  double* dts;       // last step estimate eta / sqrt(q)
+  long long* tau;    // body time (ticks)
+  long long* dt;     // current step (ticks)
+  // prediction at the block time (FP64 path reads these for all j)
+  double* pr[3];
+  double* pv[3];
+  // packed j records for the mixed path: (x_hi, y_hi, z_hi, m),
+  // (x_lo, y_lo, z_lo, 0), (vx, vy, vz, 0) as float4, 48 B per body
+  float4* jhi;
+  float4* jlo;
+  float4* jv;
+  int* act;          // active list of the step
+  int* cursor;       // per body: last previous-pass record with tau <= T
+  int* last;         // per body: its last record in the current pass
+  double* part;      // force partials [nsplit][5][n_act]
+  long long part_cap;  // doubles in part
+};
+
+struct Params {
+  double eps2;
+  double eta;
+  double inv_ticks;  // 2^-k_max (exact)
+  long long dtmax_t;
+  int k_min, k_max;
+  int precision;     // 0 FP64, 1 MIXED
+  int exact;         // FP64 single-thread ascending-j sums
+  Ctl* ctl;
+  // schedule log (device), cap == 0: off
+  int* lg_era;
+  int* lg_pass;
+  long long* lg_tau;
+  int* lg_nact;
+  int* lg_i;
+  long long* lg_dt;
+  long long lg_cap;
+};
+
+// Arguments of the force kernels (shared by the integrator and the
+// stand-alone force entry point).
+struct ForceArgs {
+  int n;
+  // FP64 structure-of-arrays j data
+  const double* m;
+  const double* x[3];
+  const double* w[3];  // velocities
+  // mixed packed j records
+  const float4* jhi;
+  const float4* jlo;
+  const float4* jv;
+  const int* idx;      // active list
+  int n_act_fixed;     // >= 0: active count; < 0: read *n_act_ptr
+  const int* n_act_ptr;
+  int* nsplit_out;     // block 0 writes the chosen split count (nullable)
+  const int* done;     // nullable; the kernel returns when *done != 0
+  double* part;        // [nsplit][5][n_act]
+  long long part_cap;  // doubles available in part
+  double eps2;
+  float eps2f;
+  int exact;           // FP64: no j-split
+};
+
+// ---------------------------------------------------------------------
+// FP64 step arithmetic, op by op.
+// ---------------------------------------------------------------------
+
+__host__ __device__ inline long long level_ticks(double x, int k_min,
+                                                 int k_max, int* underflow) {
+  // largest 2^-k <= x with k_min <= k <= k_max, in ticks (Eq. 4)
+  double p = 1.0;
+  for (int k = 0; k < k_min; ++k) p *= 0.5;
+  for (int k = k_min; k <= k_max; ++k) {
+    if (p <= x) return 1LL << (k_max - k);
+    p *= 0.5;
+  }
+  if (underflow) *underflow = 1;
+  return 1;
+}
+
+__host__ __device__ inline int level_of(long long dt_ticks, int k_max) {
+  int k = k_max;
+  while (dt_ticks > 1) {
+    dt_ticks >>= 1;
+    --k;
+  }
+  return k;
+}
+
+// first pass (standard block step): largest commensurate power of two
+// <= min(L(dts), 2d)
+__device__ inline long long forward_step(long long tau, long long d,
+                                         double dts, int k_min, int k_max,
+                                         int* uf) {
+  long long c = level_ticks(dts, k_min, k_max, uf);
+  if (c > 2 * d) c = 2 * d;
+  while (tau % c != 0) c >>= 1;
+  return c;
+}
+
+// Alg. 1 as described in its prose: even time tries 2d, d, then d/2; odd
+// time tries d, then d/2; a candidate c passes Eq. 4 when
+// c <= L((dts + dte(tau + c)) / 2).
+__device__ inline long long symmetric_step(long long tau, long long d,
+                                           double dts, double dte2,
+                                           double dte1, int k_min, int k_max,
+                                           long long dtmax_t, int* uf) {
+  const bool even = (tau % (2 * d)) == 0;
+  if (even && 2 * d <= dtmax_t &&
+      2 * d <= level_ticks(__dmul_rn(__dadd_rn(dts, dte2), 0.5), k_min,
+                           k_max, nullptr))
+    return 2 * d;
+  if (d <= level_ticks(__dmul_rn(__dadd_rn(dts, dte1), 0.5), k_min, k_max,
+                       nullptr))
+    return d;
+  if (d == 1) {
+    *uf = 1;
+    return 1;
+  }
+  return d >> 1;
+}
+
+// Eq. 2 for one component: r + v h + (0.5 a) h h and v + a h
+__device__ inline void taylor1(double r, double v, double a, double h,
+                               double& rp, double& vp) {
+  rp = __dadd_rn(__dadd_rn(r, __dmul_rn(v, h)),
+                 __dmul_rn(__dmul_rn(__dmul_rn(0.5, a), h), h));
+  vp = __dadd_rn(v, __dmul_rn(a, h));
+}
+
+// time-symmetric cubic Hermite basis on [ta, tb] at t
+struct HermiteW {
+  double h00, h10h, h01, h11h;
+};
+
+__device__ inline HermiteW hermite_weights(long long ta, long long tb,
+                                           long long t, double inv_ticks) {
+  const double x = __ddiv_rn((double)(t - ta), (double)(tb - ta));
+  const double h = __dmul_rn((double)(tb - ta), inv_ticks);
+  const double omx = __dsub_rn(1.0, x);
+  HermiteW w;
+  w.h00 = __dmul_rn(__dmul_rn(__dadd_rn(1.0, __dmul_rn(2.0, x)), omx), omx);
+  const double h10 = __dmul_rn(__dmul_rn(x, omx), omx);
+  w.h01 = __dmul_rn(__dmul_rn(x, x), __dsub_rn(3.0, __dmul_rn(2.0, x)));
+  const double h11 = __dmul_rn(__dmul_rn(x, x), __dsub_rn(x, 1.0));
+  w.h10h = __dmul_rn(h10, h);
+  w.h11h = __dmul_rn(h11, h);
+  return w;
+}
+
+__device__ inline double hermite1(const HermiteW& w, double ya, double da,
+                                  double yb, double db) {
+  return __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(w.h00, ya),
+                                       __dmul_rn(w.h10h, da)),
+                             __dmul_rn(w.h01, yb)),
+                   __dmul_rn(w.h11h, db));
+}
+
+// previous pass's step estimate of a body at tick t (linear between the
+// bracketing records; fallback past the stored records)
+__device__ inline double history_dts_at(const History& H, int start,
+                                        long long t, double fallback) {
+  int c = start;
+  if (H.tau[c] > t) return fallback;
+  for (;;) {
+    const int nx = H.next[c];
+    if (nx < 0 || H.tau[nx] > t) break;
+    c = nx;
+  }
+  if (H.tau[c] == t) return H.dts[c];
+  const int nx = H.next[c];
+  if (nx < 0) return fallback;
+  const double w = __ddiv_rn((double)(t - H.tau[c]),
+                             (double)(H.tau[nx] - H.tau[c]));
+  return __dadd_rn(H.dts[c], __dmul_rn(__dsub_rn(H.dts[nx], H.dts[c]), w));
+}
+
+// ---------------------------------------------------------------------
+// Host-side launch helpers implemented in the .cu files.
+// ---------------------------------------------------------------------
+
+// grid size and threads of the force kernels on the current device
+struct ForceLaunch {
+  int grid;
+  int threads;
+  int tile_i;          // active bodies per work item
+  long long part_cap;  // doubles of partials the grid can produce
+};
+
+ForceLaunch force_launch_shape(int precision, int device);
+cudaError_t launch_force(int precision, const ForceArgs& fa,
+                         const ForceLaunch& fl, cudaStream_t s);
+// sum nsplit partials per active body into AoS a, phi, q
+cudaError_t launch_force_finalize(const double* part, const int* nsplit,
+                                  int n_act, double* a, double* phi,
+                                  double* q, cudaStream_t s);
+// AoS (n, 3) -> packed j records for either precision
+cudaError_t launch_pack_aos(int precision, int n, const double* m,
+                            const double* r, const double* v, double* sx,
+                            double* sy, double* sz, double* sw0, double* sw1,
+                            double* sw2, double* sm, float4* jhi, float4* jlo,
+                            float4* jv, cudaStream_t s);
+
+}  // namespace tsbts

@@ -1,0 +1,28 @@
+// Launchers of the block-step kernels (k_step.cu) used by the host engine.
+#pragma once
+
+#include <climits>
+
+#include "tsbts_internal.cuh"
+
+namespace tsbts {
+
+void launch_pass_begin(Ctl* ctl, long long tau_s, long long tau_e, int pass,
+                       int era, int n, cudaStream_t s);
+void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
+                       cudaStream_t s);
+void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
+                           const History& HB, int p, cudaStream_t s);
+void launch_correct(const Bodies& B, const Params& P, const History& HA,
+                    const History& HB, int p, int grid, cudaStream_t s);
+void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s);
+void launch_next_time_extrema(const Bodies& B, Ctl* ctl, cudaStream_t s);
+void launch_load_aos(const Bodies& B, const double* m, const double* r,
+                     const double* v, Ctl* ctl, cudaStream_t s);
+void launch_init_jdata(const Bodies& B, const Params& P, cudaStream_t s);
+void launch_init_finalize(const Bodies& B, const Params& P, const int* nsplit,
+                          cudaStream_t s);
+void launch_energy(const Bodies& B, const Params& P, long long T, double* w,
+                   double* out, int sms, cudaStream_t s);
+
+}  // namespace tsbts

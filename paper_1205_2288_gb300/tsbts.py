@@ -1,0 +1,316 @@
+"""ctypes binding of the C ABI in include/tsbts.h (libtsbts.so).
+
+The functions below carry the C names and only marshal arguments; every
+step of the integrator runs in the CUDA library. There is no CPU fallback:
+loading fails loudly when the library cannot be built or loaded, and
+``tsbts_create`` fails without a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+I64 = C.c_int64
+I32P = C.POINTER(C.c_int32)
+I64P = C.POINTER(C.c_int64)
+DP = C.POINTER(C.c_double)
+VP = C.c_void_p
+
+TSBTS_OK = 0
+TSBTS_ERR_ARG = -1
+TSBTS_ERR_CUDA = -2
+TSBTS_ERR_NONFINITE = -3
+TSBTS_ERR_TIMEOUT = -4
+TSBTS_ERR_HISTORY = -6
+TSBTS_ERR_STATE = -7
+TSBTS_FP64 = 0
+TSBTS_MIXED = 1
+
+STATUS_NAMES = {0: "TSBTS_OK", -1: "TSBTS_ERR_ARG", -2: "TSBTS_ERR_CUDA",
+                -3: "TSBTS_ERR_NONFINITE", -4: "TSBTS_ERR_TIMEOUT",
+                -6: "TSBTS_ERR_HISTORY", -7: "TSBTS_ERR_STATE"}
+
+# every symbol include/tsbts.h declares
+EXPORTS = (
+    "tsbts_config_default", "tsbts_create", "tsbts_init", "tsbts_init_device",
+    "tsbts_step_era", "tsbts_energy", "tsbts_state", "tsbts_get_stats",
+    "tsbts_set_timing", "tsbts_schedule_log", "tsbts_schedule_size",
+    "tsbts_schedule_get", "tsbts_last_error", "tsbts_destroy", "tsbts_force",
+    "tsbts_release_scratch", "tsbts_version",
+)
+
+
+class tsbts_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("n_iter", C.c_int),
+                ("era_mode", C.c_int), ("era_log2", C.c_int),
+                ("dyn_min_log2", C.c_int), ("k_max", C.c_int),
+                ("exact_order", C.c_int), ("device", C.c_int),
+                ("stream", C.c_void_p), ("graph_steps", C.c_int)]
+
+
+class tsbts_stats(C.Structure):
+    _fields_ = [("block_steps", I64), ("interactions", I64), ("eras", I64),
+                ("passes", I64), ("dt_underflow", I64),
+                ("era_restarts", I64), ("history_capacity", I64),
+                ("t_sys_ticks", I64), ("force_ms", C.c_double),
+                ("force_launches", I64), ("kernel_launches", I64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TsbtsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def lib():
+    """Load (building first if needed) libtsbts.so and declare signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        L = C.CDLL(_build.build())
+        L.tsbts_config_default.argtypes = [C.POINTER(tsbts_config)]
+        L.tsbts_config_default.restype = None
+        L.tsbts_create.argtypes = [C.POINTER(VP), C.POINTER(tsbts_config)]
+        L.tsbts_init.argtypes = [VP, I64, DP, DP, DP, C.c_double, C.c_double,
+                                 C.c_double]
+        L.tsbts_init_device.argtypes = [VP, I64, VP, VP, VP, C.c_double,
+                                        C.c_double, C.c_double]
+        L.tsbts_step_era.argtypes = [VP, C.c_double, DP]
+        L.tsbts_energy.argtypes = [VP, DP, DP, DP]
+        L.tsbts_state.argtypes = [VP, DP, DP, DP, DP, DP, I64P, I64P]
+        L.tsbts_get_stats.argtypes = [VP, C.POINTER(tsbts_stats)]
+        L.tsbts_set_timing.argtypes = [VP, C.c_int]
+        L.tsbts_schedule_log.argtypes = [VP, I64]
+        L.tsbts_schedule_size.argtypes = [VP, I64P, I64P, I64P]
+        L.tsbts_schedule_get.argtypes = [VP, I32P, I32P, I64P, I32P, I32P,
+                                         I64P]
+        L.tsbts_last_error.argtypes = [VP]
+        L.tsbts_last_error.restype = C.c_char_p
+        L.tsbts_destroy.argtypes = [VP]
+        L.tsbts_destroy.restype = None
+        L.tsbts_force.argtypes = [C.c_int, C.c_int, I64, VP, VP, VP,
+                                  C.c_double, I64, VP, VP, VP, VP, VP]
+        L.tsbts_release_scratch.argtypes = []
+        L.tsbts_version.argtypes = []
+        L.tsbts_version.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def _p(x, t=DP):
+    return x.ctypes.data_as(t)
+
+
+def _check(code, ctx=None):
+    if code != TSBTS_OK:
+        msg = ""
+        if ctx:
+            m = lib().tsbts_last_error(ctx)
+            msg = m.decode() if m else ""
+        raise TsbtsError(code, msg)
+
+
+# --- thin wrappers with the C names -------------------------------------
+
+def tsbts_config_default() -> tsbts_config:
+    cfg = tsbts_config()
+    lib().tsbts_config_default(C.byref(cfg))
+    return cfg
+
+
+def tsbts_create(cfg: tsbts_config):
+    h = VP()
+    _check(lib().tsbts_create(C.byref(h), C.byref(cfg)))
+    return h
+
+
+def tsbts_init(ctx, m, r, v, eps, eta, dt_max):
+    m = np.ascontiguousarray(m, np.float64)
+    r = np.ascontiguousarray(r, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    n = m.shape[0]
+    if r.shape != (n, 3) or v.shape != (n, 3):
+        raise ValueError("r and v must have shape (n, 3)")
+    _check(lib().tsbts_init(ctx, n, _p(m), _p(r), _p(v), float(eps),
+                            float(eta), float(dt_max)), ctx)
+
+
+def tsbts_init_device(ctx, m, r, v, eps, eta, dt_max):
+    """m, r, v: contiguous float64 CUDA tensors of shape (n,), (n,3), (n,3)."""
+    n = m.shape[0]
+    _check(lib().tsbts_init_device(ctx, n, m.data_ptr(), r.data_ptr(),
+                                   v.data_ptr(), float(eps), float(eta),
+                                   float(dt_max)), ctx)
+
+
+def tsbts_step_era(ctx, t_end) -> float:
+    t = C.c_double()
+    _check(lib().tsbts_step_era(ctx, float(t_end), C.byref(t)), ctx)
+    return t.value
+
+
+def tsbts_energy(ctx):
+    ek, ep, et = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().tsbts_energy(ctx, C.byref(ek), C.byref(ep), C.byref(et)),
+           ctx)
+    return ek.value, ep.value, et.value
+
+
+def tsbts_state(ctx, n):
+    t = C.c_double()
+    m = np.zeros(n)
+    r, v, a = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    tau, dt = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    _check(lib().tsbts_state(ctx, C.byref(t), _p(m), _p(r), _p(v), _p(a),
+                             _p(tau, I64P), _p(dt, I64P)), ctx)
+    return dict(t=t.value, m=m, r=r, v=v, a=a, tau=tau, dt=dt)
+
+
+def tsbts_get_stats(ctx) -> dict:
+    s = tsbts_stats()
+    _check(lib().tsbts_get_stats(ctx, C.byref(s)), ctx)
+    return s.as_dict()
+
+
+def tsbts_set_timing(ctx, enable: bool):
+    _check(lib().tsbts_set_timing(ctx, 1 if enable else 0), ctx)
+
+
+def tsbts_schedule_log(ctx, capacity: int):
+    _check(lib().tsbts_schedule_log(ctx, int(capacity)), ctx)
+
+
+def tsbts_schedule_get(ctx):
+    L = lib()
+    ns, ne, dr = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(L.tsbts_schedule_size(ctx, C.byref(ns), C.byref(ne), C.byref(dr)),
+           ctx)
+    ns, ne = ns.value, ne.value
+    era = np.zeros(ns, np.int32)
+    pas = np.zeros(ns, np.int32)
+    tau = np.zeros(ns, np.int64)
+    nact = np.zeros(ns, np.int32)
+    ei = np.zeros(ne, np.int32)
+    edt = np.zeros(ne, np.int64)
+    _check(L.tsbts_schedule_get(ctx, _p(era, I32P), _p(pas, I32P),
+                                _p(tau, I64P), _p(nact, I32P), _p(ei, I32P),
+                                _p(edt, I64P)), ctx)
+    return dict(era=era, pass_=pas, tau=tau, n_act=nact, idx=ei, dt=edt,
+                dropped=dr.value)
+
+
+def tsbts_destroy(ctx):
+    if ctx:
+        lib().tsbts_destroy(ctx)
+
+
+def tsbts_force(precision, m, r, v, eps, idx, a, phi, q, exact_order=-1,
+                stream=None):
+    """Device-pointer force call on torch CUDA tensors (see tsbts.h)."""
+    import torch
+    for t in (m, r, v, idx, a, phi, q):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("tsbts_force takes contiguous CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream(m.device).cuda_stream
+    _check(lib().tsbts_force(int(precision), int(exact_order), m.shape[0],
+                             m.data_ptr(), r.data_ptr(), v.data_ptr(),
+                             float(eps), idx.shape[0], idx.data_ptr(),
+                             a.data_ptr(), phi.data_ptr(), q.data_ptr(),
+                             stream))
+
+
+def tsbts_version() -> str:
+    return lib().tsbts_version().decode()
+
+
+# --- convenience wrapper --------------------------------------------------
+
+class Simulation:
+    """One TSBTS context: init -> step_era -> energy/state (include/tsbts.h).
+
+    All arrays are numpy float64 on the host; the integration runs on the
+    GPU.
+    """
+
+    def __init__(self, m, r, v, *, eps, eta, dt_max, precision=TSBTS_FP64,
+                 n_iter=3, era_mode=0, era_log2=3, dyn_min_log2=3, k_max=20,
+                 exact_order=-1, device=0, stream=None, graph_steps=32):
+        cfg = tsbts_config_default()
+        cfg.precision = precision
+        cfg.n_iter = n_iter
+        cfg.era_mode = era_mode
+        cfg.era_log2 = era_log2
+        cfg.dyn_min_log2 = dyn_min_log2
+        cfg.k_max = k_max
+        cfg.exact_order = exact_order
+        cfg.device = device
+        cfg.stream = stream
+        cfg.graph_steps = graph_steps
+        self.cfg = cfg
+        self.k_max = k_max
+        self.n = int(np.asarray(m).shape[0])
+        self.ctx = tsbts_create(cfg)
+        try:
+            tsbts_init(self.ctx, m, r, v, eps, eta, dt_max)
+        except Exception:
+            tsbts_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def step_era(self, t_end):
+        return tsbts_step_era(self.ctx, t_end)
+
+    run = step_era
+
+    def energy(self):
+        ek, ep, _ = tsbts_energy(self.ctx)
+        return ek, ep
+
+    def state(self):
+        return tsbts_state(self.ctx, self.n)
+
+    def stats(self):
+        return tsbts_get_stats(self.ctx)
+
+    def set_timing(self, enable=True):
+        tsbts_set_timing(self.ctx, enable)
+
+    def schedule_log(self, capacity):
+        tsbts_schedule_log(self.ctx, capacity)
+
+    def schedule(self):
+        return tsbts_schedule_get(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            tsbts_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

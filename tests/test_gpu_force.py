@@ -1,0 +1,142 @@
+"""Parity of the CUDA force kernels (Alg. 2 step 5, Eq. 3, Plummer
+softening) with the FP64 oracle, through the C ABI entry tsbts_force.
+
+FP64 with ascending-j order is bit-identical to the oracle; the FP64 j-split
+differs only in summation order; the mixed path (FP32 pair terms on
+double-single coordinates) must keep every a_i within 1e-6 of the
+oracle relative to the sum of the pair magnitudes sum_j m_j / s_ij^2, the
+bulk of |a_i| relative errors below 1e-6, phi within 1e-6 relative and q
+(an exact FP32 max of FP32 pair terms) within 2e-6 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_1205_2288_gb300 import inputs, tsbts
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    return torch
+
+
+def gpu_force(torch, precision, m, r, v, eps, idx, exact_order=-1):
+    dev = "cuda:0"
+    tm = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+    tr = torch.from_numpy(np.ascontiguousarray(r)).to(dev)
+    tv = torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+    ti = torch.from_numpy(np.ascontiguousarray(idx, np.int32)).to(dev)
+    na = len(idx)
+    a = torch.full((na, 3), float("nan"), dtype=torch.float64, device=dev)
+    phi = torch.full((na,), float("nan"), dtype=torch.float64, device=dev)
+    q = torch.full((na,), float("nan"), dtype=torch.float64, device=dev)
+    tsbts.tsbts_force(precision, tm, tr, tv, eps, ti, a, phi, q,
+                      exact_order=exact_order)
+    torch.cuda.synchronize()
+    return a.cpu().numpy(), phi.cpu().numpy(), q.cpu().numpy()
+
+
+def pair_magnitude_sum(m, r, eps, idx):
+    """sum_j m_j / s_ij^2 per active body (the scale of a_i's terms)."""
+    out = np.zeros(len(idx))
+    for k, i in enumerate(idx):
+        d2 = ((r - r[i]) ** 2).sum(1) + eps ** 2
+        w = m / d2
+        w[i] = 0.0
+        out[k] = w.sum()
+    return out
+
+
+CASES = [  # (n, n_act, eps, seed): ragged n, tiny and full active sets
+    (1000, 1000, 0.01, 0),
+    (1000, 1, 0.01, 1),
+    (1000, 37, 0.0, 2),
+    (777, 700, 1 / 256, 3),
+    (4099, 129, 0.01, 4),
+]
+
+
+@pytest.mark.parametrize("n,n_act,eps,seed", CASES)
+def test_fp64_ascending_order_is_bit_identical(torch_cuda, orc, n, n_act, eps,
+                                               seed):
+    m, r, v = inputs.plummer(n, seed)
+    idx = inputs.active_subset(n, n_act, seed + 100)
+    a, phi, q = gpu_force(torch_cuda, tsbts.TSBTS_FP64, m, r, v, eps, idx,
+                          exact_order=1)
+    ao, phio, qo = orc.forces(m, r, v, eps, idx)
+    np.testing.assert_array_equal(a, ao)
+    np.testing.assert_array_equal(phi, phio)
+    np.testing.assert_array_equal(q, qo)
+
+
+@pytest.mark.parametrize("n,n_act,eps,seed", CASES + [(20000, 3, 0.01, 5)])
+def test_fp64_jsplit_matches_to_rounding(torch_cuda, orc, n, n_act, eps, seed):
+    m, r, v = inputs.plummer(n, seed)
+    idx = inputs.active_subset(n, n_act, seed + 100)
+    a, phi, q = gpu_force(torch_cuda, tsbts.TSBTS_FP64, m, r, v, eps, idx,
+                          exact_order=0)
+    ao, phio, qo = orc.forces(m, r, v, eps, idx)
+    scale = pair_magnitude_sum(m, r, eps, idx)
+    assert (np.abs(a - ao).max(1) / scale).max() < 1e-13
+    np.testing.assert_allclose(phi, phio, rtol=1e-13)
+    # q is a max of identically rounded pair terms: exact in any order
+    np.testing.assert_array_equal(q, qo)
+
+
+@pytest.mark.parametrize("n,n_act,eps,seed", CASES + [(20000, 3, 0.01, 5),
+                                                      (20000, 5000, 1 / 512, 6)])
+def test_mixed_within_tolerance(torch_cuda, orc, n, n_act, eps, seed):
+    m, r, v = inputs.plummer(n, seed)
+    idx = inputs.active_subset(n, n_act, seed + 100)
+    a, phi, q = gpu_force(torch_cuda, tsbts.TSBTS_MIXED, m, r, v, eps, idx)
+    ao, phio, qo = orc.forces(m, r, v, eps, idx)
+    scale = pair_magnitude_sum(m, r, eps, idx)
+    err_scaled = np.abs(a - ao).max(1) / scale
+    assert err_scaled.max() < 1e-6
+    rel = np.linalg.norm(a - ao, axis=1) / np.linalg.norm(ao, axis=1)
+    assert np.quantile(rel, 0.99) < 1e-6
+    np.testing.assert_allclose(phi, phio, rtol=1e-6)
+    np.testing.assert_allclose(q, qo, rtol=2e-6)
+
+
+def test_edge_cases(torch_cuda, orc):
+    torch = torch_cuda
+    # one body: no pair, all zeros
+    m, r, v = np.array([0.5]), np.array([[0.1, 0.2, 0.3]]), np.zeros((1, 3))
+    for prec in (tsbts.TSBTS_FP64, tsbts.TSBTS_MIXED):
+        a, phi, q = gpu_force(torch, prec, m, r, v, 0.01, np.array([0]))
+        assert np.all(a == 0) and phi[0] == 0 and q[0] == 0
+    # repeated active indices give repeated rows
+    m, r, v = inputs.plummer(300, 9)
+    idx = np.array([5, 5, 17, 5], np.int32)
+    for prec in (tsbts.TSBTS_FP64, tsbts.TSBTS_MIXED):
+        a, phi, q = gpu_force(torch, prec, m, r, v, 0.01, idx)
+        np.testing.assert_array_equal(a[0], a[1])
+        np.testing.assert_array_equal(a[0], a[3])
+    # empty active set is a no-op
+    tm = torch.zeros(4, dtype=torch.float64, device="cuda:0")
+    tr = torch.zeros(4, 3, dtype=torch.float64, device="cuda:0")
+    e = torch.zeros(0, dtype=torch.int32, device="cuda:0")
+    z = torch.zeros(0, dtype=torch.float64, device="cuda:0")
+    tsbts.tsbts_force(0, tm, tr, tr, 0.1, e, z.view(0, 3), z, z)
+
+
+def test_full_size_sampled(torch_cuda, orc):
+    """Plummer n = 131072, eps = 1/512: the active-set sweep of the force
+    benchmark; 48 sampled outputs per set are checked against the oracle."""
+    n, eps = 131072, 1 / 512
+    m, r, v = inputs.plummer(n, 0)
+    for n_act in (1, 32, 1024, 32768, n):
+        idx = inputs.active_subset(n, n_act, 1000 + n_act)
+        a, phi, q = gpu_force(torch_cuda, tsbts.TSBTS_MIXED, m, r, v, eps, idx)
+        pick = np.unique(np.linspace(0, n_act - 1, 48).astype(int))
+        ao, phio, qo = orc.forces(m, r, v, eps, idx[pick])
+        scale = pair_magnitude_sum(m, r, eps, idx[pick])
+        assert (np.abs(a[pick] - ao).max(1) / scale).max() < 1e-6
+        np.testing.assert_allclose(phi[pick], phio, rtol=1e-6)
+        np.testing.assert_allclose(q[pick], qo, rtol=2e-6)
+        assert np.isfinite(a).all() and np.isfinite(phi).all()
