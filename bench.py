@@ -213,6 +213,54 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def force_sweep(args):
+    """Force kernel alone (tsbts_force, device pointers): Plummer n = 131072,
+    eps = 1/512, seeded random active sets of the given sizes."""
+    import numpy as np
+    import torch
+
+    from paper_1205_2288_gb300 import inputs, tsbts
+
+    n, eps = 131072, 1.0 / 512.0
+    dev = torch.device("cuda", 0)
+    m, r, v = inputs.plummer(n, SEED)
+    dm = torch.from_numpy(m).to(dev)
+    dr = torch.from_numpy(r).to(dev)
+    dv = torch.from_numpy(v).to(dev)
+    sizes = [int(x) for x in args.n_act.split(",")] if args.n_act else \
+        [1, 32, 1024, 32768, n]
+    precs = [tsbts.TSBTS_MIXED] + ([] if args.no_fp64 else [tsbts.TSBTS_FP64])
+    out = {}
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2070e6 / OPS_PER_INTERACTION
+    for prec in precs:
+        for na in sizes:
+            idx = torch.from_numpy(inputs.active_subset(n, na, 1000 + na)).to(dev)
+            a = torch.empty(na, 3, dtype=torch.float64, device=dev)
+            phi = torch.empty(na, dtype=torch.float64, device=dev)
+            q = torch.empty(na, dtype=torch.float64, device=dev)
+            reps = args.steps if prec == tsbts.TSBTS_MIXED else 1
+            for _ in range(args.warmup if prec == tsbts.TSBTS_MIXED else 1):
+                tsbts.tsbts_force(prec, dm, dr, dv, eps, idx, a, phi, q)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                tsbts.tsbts_force(prec, dm, dr, dv, eps, idx, a, phi, q)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gint = na * n / (ms / 1e3) / 1e9
+            key = ("mixed" if prec else "fp64") + f"_nact{na}"
+            out[key] = {"ms_per_call": ms, "Ginteractions_s": gint,
+                        "frac_of_fp32_roofline": gint * 1e9 / peak}
+    line = {"metric": "force kernel sweep (tsbts_force), Plummer n=131072, "
+                      "eps=1/512", "unit": "Ginteractions/s",
+            "peak_Ginteractions_s": peak / 1e9, "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,7 +270,13 @@ def main():
     ap.add_argument("--t-end", type=float, default=T_END)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--force-sweep", action="store_true",
+                    help="time the force kernel alone on n = 131072")
+    ap.add_argument("--n-act", default="",
+                    help="comma-separated active-set sizes for --force-sweep")
     args = ap.parse_args()
+    if args.force_sweep:
+        return force_sweep(args)
     ws, rank, local = dist_env()
     dist = init_dist(ws)
     if args.impl == "reference":
@@ -360,11 +414,6 @@ def main():
     if rank == 0:
         # the plain FP64 GPU path on a bounded sample of the same workload
         if not args.no_fp64:
-            cfg64 = tsbts.tsbts_config_default()
-            cfg64.precision = tsbts.TSBTS_FP64
-            cfg64.n_iter = N_ITER
-            cfg64.era_mode = 1
-            cfg64.device = local
             sim = tsbts.Simulation(m, r, v, eps=EPS, eta=ETA, dt_max=DT_MAX,
                                    precision=tsbts.TSBTS_FP64, n_iter=N_ITER,
                                    era_mode=1, device=local)

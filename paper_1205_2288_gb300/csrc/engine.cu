@@ -63,6 +63,7 @@ struct tsbts_ctx {
   double* d_w = nullptr;
   double* d_eout = nullptr;
   int* d_nsplit = nullptr;  // scratch for init's split count
+  Plan* d_plans = nullptr;  // force work plan per active count
   ForceLaunch fl{};
   int correct_grid = 1;
   // counters
@@ -185,18 +186,43 @@ ForceArgs force_args_engine(tsbts_ctx* c, int p) {
   fa.eps2 = c->eps * c->eps;
   fa.eps2f = (float)(c->eps * c->eps);
   fa.exact = c->exact;
+  fa.plans = c->d_plans;
   return fa;
 }
 
-// one block step: A (select + predict), B (force), C (correct)
-void enqueue_step(tsbts_ctx* c, int p, int ev_slot) {
+// work plan of the force kernel for every active count 0..n, chosen on the
+// host (device memory: 16 B per body; above 2^20 bodies the kernel chooses
+// its plan itself)
+void build_plan_table(tsbts_ctx* c) {
+  c->d_plans = nullptr;
+  if (c->n > (1 << 20)) return;
+  std::vector<Plan> t(c->n + 1);
+  for (int k = 0; k <= c->n; ++k)
+    t[k] = plan_force(c->cfg.precision, c->exact, k, c->n, c->fl.grid,
+                      c->B.part_cap);
+  c->d_plans = dalloc<Plan>(c->allocs, t.size());
+  ck(cudaMemcpyAsync(c->d_plans, t.data(), sizeof(Plan) * t.size(),
+                     cudaMemcpyHostToDevice, c->s),
+     "copy plans");
+  ck(cudaStreamSynchronize(c->s), "synchronize");
+}
+
+// one block step: A (select + predict), B (force), C (correct). Timing
+// events inside a captured graph are external event nodes, so that they
+// are recorded (and timed) at every replay.
+void enqueue_step(tsbts_ctx* c, int p, int ev_slot, bool capturing) {
   const History& HA = c->H[0];
   const History& HB = c->H[1];
+  const unsigned evflags =
+      capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   launch_select_predict(c->B, c->P, HA, HB, p, c->s);
-  if (ev_slot >= 0) ck(cudaEventRecord(c->ev[2 * ev_slot], c->s), "event");
+  if (ev_slot >= 0)
+    ck(cudaEventRecordWithFlags(c->ev[2 * ev_slot], c->s, evflags), "event");
   ck(launch_force(c->cfg.precision, force_args_engine(c, p), c->fl, c->s),
      "force launch");
-  if (ev_slot >= 0) ck(cudaEventRecord(c->ev[2 * ev_slot + 1], c->s), "event");
+  if (ev_slot >= 0)
+    ck(cudaEventRecordWithFlags(c->ev[2 * ev_slot + 1], c->s, evflags),
+       "event");
   launch_correct(c->B, c->P, HA, HB, p, c->correct_grid, c->s);
 }
 
@@ -216,7 +242,8 @@ void build_graph(tsbts_ctx* c) {
   ck(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal),
      "begin capture");
   try {
-    for (int k = 0; k < G; ++k) enqueue_step(c, k & 1, c->timing ? k : -1);
+    for (int k = 0; k < G; ++k)
+      enqueue_step(c, k & 1, c->timing ? k : -1, true);
   } catch (...) {
     cudaStreamEndCapture(c->s, &g);
     throw;
@@ -277,7 +304,7 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
     for (;;) {
       if (c->timing) ensure_events(c, (int)chunk);
       for (long long k = 0; k < chunk; ++k) {
-        enqueue_step(c, p, c->timing ? (int)k : -1);
+        enqueue_step(c, p, c->timing ? (int)k : -1, false);
         c->launches += 3;
         p ^= 1;
       }
@@ -386,6 +413,9 @@ void setup_bodies(tsbts_ctx* c, int n) {
   B.act = dalloc<int>(L, n);
   B.cursor = dalloc<int>(L, n);
   B.last = dalloc<int>(L, n);
+  B.seg_ta = dalloc<long long>(L, n);
+  B.seg_tb = dalloc<long long>(L, n);
+  B.seg = dalloc<double>(L, 18 * (size_t)n);
   B.part_cap = std::max<long long>(c->fl.part_cap, 5LL * n);
   B.part = dalloc<double>(L, B.part_cap);
   Bodies& S = c->snap;
@@ -445,8 +475,10 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
                (c->cfg.exact_order == 1 ||
                 (c->cfg.exact_order < 0 && n <= 8192));
     c->fl = force_launch_shape(c->cfg.precision, c->cfg.device);
-    c->correct_grid = std::max(1, std::min(c->sms * 8, (c->n + 127) / 128));
+    // 32-thread blocks spread the FP64 work of small active sets over SMs
+    c->correct_grid = std::max(1, std::min(c->sms * 32, (c->n + 31) / 32));
     setup_bodies(c, (int)n);
+    build_plan_table(c);
     Params& P = c->P;
     P = Params{};
     P.eps2 = eps * eps;
@@ -490,6 +522,19 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     free_list(tmp);
     if (c->h_ctl->err & kErrNonFinite)
       return fail(c, TSBTS_ERR_NONFINITE, "non-finite input or initial force");
+    if (c->cfg.precision == TSBTS_MIXED && c->d_plans) {
+      // measured work plans on this device for this n (first context only;
+      // later contexts reuse the cached table)
+      std::vector<Plan> t;
+      ForceArgs base = force_args_engine(c, 0);
+      ck(autotune_mixed_plans(c->cfg.device, base, c->fl, c->d_nsplit, c->s,
+                              &t),
+         "force plan autotuning");
+      ck(cudaMemcpyAsync(c->d_plans, t.data(), sizeof(Plan) * t.size(),
+                         cudaMemcpyHostToDevice, c->s),
+         "copy plans");
+      ck(cudaStreamSynchronize(c->s), "synchronize");
+    }
     c->inited = true;
     c->graph_dirty = true;
     return TSBTS_OK;
@@ -517,6 +562,7 @@ struct Scratch {
   float4* j4 = nullptr;   // 3 n float4
   double* part = nullptr;
   int* nsplit = nullptr;
+  int* iota = nullptr;    // 0, 1, ..., n_cap - 1 (active list for tuning)
 };
 std::mutex g_scratch_mu;
 std::vector<Scratch> g_scratch;
@@ -827,19 +873,29 @@ int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
     std::lock_guard<std::mutex> g(g_scratch_mu);
     if ((int)g_scratch.size() <= dev) g_scratch.resize(dev + 1);
     Scratch& S = g_scratch[dev];
-    const long long need_part = std::max<long long>(fl.part_cap, 5LL * n_act);
+    // partial sums of up to n active bodies: the plan tuner times active
+    // counts up to n, whatever this call's n_act
+    const long long need_part =
+        std::max<long long>(fl.part_cap, 5LL * std::max<int64_t>(n_act, n));
     if (S.n_cap < n || S.part_cap < need_part) {
       ck(cudaDeviceSynchronize(), "synchronize before scratch growth");
       cudaFree(S.soa);
       cudaFree(S.j4);
       cudaFree(S.part);
       cudaFree(S.nsplit);
+      cudaFree(S.iota);
       S = Scratch{};
       const int ncap = (int)std::max<int64_t>(n, S.n_cap);
       ck(cudaMalloc(&S.soa, sizeof(double) * 7 * (size_t)ncap), "scratch");
       ck(cudaMalloc(&S.j4, sizeof(float4) * 3 * (size_t)ncap), "scratch");
       ck(cudaMalloc(&S.part, sizeof(double) * need_part), "scratch");
       ck(cudaMalloc(&S.nsplit, sizeof(int)), "scratch");
+      ck(cudaMalloc(&S.iota, sizeof(int) * (size_t)ncap), "scratch");
+      std::vector<int> iota(ncap);
+      for (int k = 0; k < ncap; ++k) iota[k] = k;
+      ck(cudaMemcpy(S.iota, iota.data(), sizeof(int) * (size_t)ncap,
+                    cudaMemcpyHostToDevice),
+         "scratch");
       S.n_cap = ncap;
       S.part_cap = need_part;
     }
@@ -869,6 +925,24 @@ int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
     fa.eps2f = (float)(eps * eps);
     fa.exact = precision == TSBTS_FP64 &&
                (exact_order == 1 || (exact_order < 0 && n <= 8192));
+    fa.plan = plan_force(precision, fa.exact, (int)n_act, ni, fl.grid,
+                         S.part_cap);
+    if (precision == TSBTS_MIXED && ni <= (1 << 20)) {
+      // measured plans: the first call for a new n tunes them on these j
+      // records and caches the table for the process
+      const std::vector<Plan>* tp = tuned_plans(dev, ni, fl.grid);
+      if (!tp) {
+        std::vector<Plan> t;
+        ForceArgs base = fa;
+        base.idx = S.iota;
+        ck(autotune_mixed_plans(dev, base, fl, S.nsplit, s, &t),
+           "force plan autotuning");
+        tp = tuned_plans(dev, ni, fl.grid);
+      }
+      if (tp && (long long)(*tp)[n_act].S * 5 * n_act <= S.part_cap)
+        fa.plan = (*tp)[n_act];
+    }
+    fa.has_plan = 1;
     ck(launch_force(precision, fa, fl, s), "force");
     ck(launch_force_finalize(S.part, S.nsplit, (int)n_act, a, phi, q, s),
        "force finalize");
@@ -891,6 +965,7 @@ int tsbts_release_scratch(void) {
   cudaFree(S.j4);
   cudaFree(S.part);
   cudaFree(S.nsplit);
+  cudaFree(S.iota);
   S = Scratch{};
   return TSBTS_OK;
 }

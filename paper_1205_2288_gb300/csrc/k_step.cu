@@ -57,6 +57,7 @@ __global__ void pass_setup_kernel(Bodies B, Params P, History cur) {
     cur.next[i] = -1;
     B.last[i] = i;
     B.cursor[i] = i;
+    B.seg_ta[i] = LLONG_MAX;
     atomicAdd(&h[level_of(B.dt[i], P.k_max)], 1);
   }
   __syncthreads();
@@ -92,26 +93,28 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
   __shared__ long long s_tn;
   __shared__ int s_stop;
   Ctl* ctl = P.ctl;
-  if (threadIdx.x == 0) {
-    int stop = ctl->done ? 3 : 0;
-    long long tn = 0;
-    if (!stop) {
-      int kk = -1;
-      for (int k = P.k_max; k >= 0; --k)
-        if (ctl->hist[k] > 0) {
-          kk = k;
-          break;
+  if (threadIdx.x < 32) {
+    // smallest populated step = highest populated level, one warp-wide load
+    const int lane = threadIdx.x;
+    const int h0 = ctl->hist[lane], h1 = ctl->hist[lane + 32];
+    const unsigned b0 = __ballot_sync(kFull, h0 > 0 && lane <= P.k_max);
+    const unsigned b1 = __ballot_sync(kFull, h1 > 0 && lane + 32 <= P.k_max);
+    if (lane == 0) {
+      int stop = ctl->done ? 3 : 0;
+      long long tn = 0;
+      if (!stop) {
+        const int kk = b1 ? 63 - __clz(b1) : (b0 ? 31 - __clz(b0) : -1);
+        if (kk < 0) {
+          stop = 1;
+        } else {
+          const long long D = 1LL << (P.k_max - kk);
+          tn = (ctl->slot[p].tau_c / D + 1) * D;
+          if (tn > ctl->tau_e) stop = 2;
         }
-      if (kk < 0) {
-        stop = 1;
-      } else {
-        const long long D = 1LL << (P.k_max - kk);
-        tn = (ctl->slot[p].tau_c / D + 1) * D;
-        if (tn > ctl->tau_e) stop = 2;
       }
+      s_tn = tn;
+      s_stop = stop;
     }
-    s_tn = tn;
-    s_stop = stop;
   }
   __syncthreads();
   if (s_stop) {
@@ -135,34 +138,54 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
     double rp[3], vp[3];
     bool have = false;
     if (pass > 0 && !act) {
-      int c = B.cursor[j];
-      if (prev.tau[c] <= tn) {
-        for (;;) {
+      // previous-pass records A <= tn < B of body j, from the segment cache;
+      // refilled from the history chain only when tn leaves the segment
+      const int n = B.n;
+      long long ta = B.seg_ta[j], tb = B.seg_tb[j];
+      if (!(ta <= tn && (tb < 0 || tn < tb))) {
+        int c = B.cursor[j];
+        if (prev.tau[c] <= tn) {
+          for (;;) {
+            const int nx = prev.next[c];
+            if (nx < 0 || prev.tau[nx] > tn) break;
+            c = nx;
+          }
+          B.cursor[j] = c;
           const int nx = prev.next[c];
-          if (nx < 0 || prev.tau[nx] > tn) break;
-          c = nx;
-        }
-        B.cursor[j] = c;
-        if (prev.tau[c] == tn) {
+          ta = prev.tau[c];
+          tb = nx >= 0 ? prev.tau[nx] : -1;
           for (int d = 0; d < 3; ++d) {
-            rp[d] = prev.r[d][c];
-            vp[d] = prev.v[d][c];
-          }
-          have = true;
-        } else {
-          const int nx = prev.next[c];
-          if (nx >= 0) {
-            const HermiteW w =
-                hermite_weights(prev.tau[c], prev.tau[nx], tn, P.inv_ticks);
-            for (int d = 0; d < 3; ++d) {
-              rp[d] = hermite1(w, prev.r[d][c], prev.v[d][c], prev.r[d][nx],
-                               prev.v[d][nx]);
-              vp[d] = hermite1(w, prev.v[d][c], prev.a[d][c], prev.v[d][nx],
-                               prev.a[d][nx]);
+            B.seg[(d + 0) * n + j] = prev.r[d][c];
+            B.seg[(d + 3) * n + j] = prev.v[d][c];
+            B.seg[(d + 6) * n + j] = prev.a[d][c];
+            if (nx >= 0) {
+              B.seg[(d + 9) * n + j] = prev.r[d][nx];
+              B.seg[(d + 12) * n + j] = prev.v[d][nx];
+              B.seg[(d + 15) * n + j] = prev.a[d][nx];
             }
-            have = true;
           }
+        } else {
+          ta = LLONG_MAX;  // no record at or before tn: Taylor
+          tb = -1;
         }
+        B.seg_ta[j] = ta;
+        B.seg_tb[j] = tb;
+      }
+      if (ta == tn) {
+        for (int d = 0; d < 3; ++d) {
+          rp[d] = B.seg[(d + 0) * n + j];
+          vp[d] = B.seg[(d + 3) * n + j];
+        }
+        have = true;
+      } else if (ta < tn && tb > tn) {
+        const HermiteW w = hermite_weights(ta, tb, tn, P.inv_ticks);
+        for (int d = 0; d < 3; ++d) {
+          rp[d] = hermite1(w, B.seg[(d + 0) * n + j], B.seg[(d + 3) * n + j],
+                           B.seg[(d + 9) * n + j], B.seg[(d + 12) * n + j]);
+          vp[d] = hermite1(w, B.seg[(d + 3) * n + j], B.seg[(d + 6) * n + j],
+                           B.seg[(d + 12) * n + j], B.seg[(d + 15) * n + j]);
+        }
+        have = true;
       }
     }
     if (!have) {
@@ -189,6 +212,9 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
                                int p) {
   Ctl* ctl = P.ctl;
   if (ctl->done) return;
+  __shared__ int dh[kMaxLevels];
+  for (int t = threadIdx.x; t < kMaxLevels; t += blockDim.x) dh[t] = 0;
+  __syncthreads();
   const StepSlot sl = ctl->slot[p];
   const int n_act = sl.cnt;
   const long long tn = sl.tau_next;
@@ -206,6 +232,7 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
       an[1] = pp[1 * n_act + k];
       an[2] = pp[2 * n_act + k];
       q = pp[4 * n_act + k];
+      #pragma unroll 4
       for (int sp = 1; sp < S; ++sp) {
         pp = B.part + (long long)sp * 5 * n_act;
         an[0] = __dadd_rn(an[0], pp[0 * n_act + k]);
@@ -254,7 +281,17 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
     if (pass == 0) {
       c = forward_step(tn, d, dts, P.k_min, P.k_max, &uf);
     } else {
-      const int start = B.cursor[i];
+      // advance the body's previous-pass cursor to the block time so that
+      // the lookups below walk only the records of this step
+      int start = B.cursor[i];
+      if (prev.tau[start] <= tn) {
+        for (;;) {
+          const int nx = prev.next[start];
+          if (nx < 0 || prev.tau[nx] > tn) break;
+          start = nx;
+        }
+        B.cursor[i] = start;
+      }
       const double e2 = history_dts_at(prev, start, tn + 2 * d, dts);
       const double e1 = history_dts_at(prev, start, tn + d, dts);
       c = symmetric_step(tn, d, dts, e2, e1, P.k_min, P.k_max, P.dtmax_t,
@@ -262,8 +299,8 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
     }
     if (uf) atomicAdd(&ctl->underflow, 1ULL);
     if (c != d) {
-      atomicSub(&ctl->hist[level_of(d, P.k_max)], 1);
-      atomicAdd(&ctl->hist[level_of(c, P.k_max)], 1);
+      atomicSub(&dh[level_of(d, P.k_max)], 1);
+      atomicAdd(&dh[level_of(c, P.k_max)], 1);
     }
     B.dt[i] = c;
     if (P.lg_cap > 0) {
@@ -274,6 +311,10 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
       }
     }
   }
+  // level-count changes of this block, one global atomic per changed level
+  __syncthreads();
+  for (int t = threadIdx.x; t <= P.k_max; t += blockDim.x)
+    if (dh[t]) atomicAdd(&ctl->hist[t], dh[t]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     StepSlot& nx = ctl->slot[p ^ 1];
     nx.tau_c = tn;
@@ -385,6 +426,7 @@ __global__ void init_finalize_kernel(Bodies B, Params P, const int* nsplit) {
     an[1] = B.part[1 * n + i];
     an[2] = B.part[2 * n + i];
     q = B.part[4 * n + i];
+    #pragma unroll 4
     for (int sp = 1; sp < S; ++sp) {
       const double* pp = B.part + (long long)sp * 5 * n;
       an[0] = __dadd_rn(an[0], pp[0 * n + i]);
@@ -494,12 +536,13 @@ void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
 
 void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
                            const History& HB, int p, cudaStream_t s) {
-  select_predict_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, P, HA, HB, p);
+  select_predict_kernel<<<grid_for(B.n, 128, 1 << 30), 128, 0, s>>>(B, P, HA, HB,
+                                                                  p);
 }
 
 void launch_correct(const Bodies& B, const Params& P, const History& HA,
                     const History& HB, int p, int grid, cudaStream_t s) {
-  correct_kernel<<<grid, 128, 0, s>>>(B, P, HA, HB, p);
+  correct_kernel<<<grid, 32, 0, s>>>(B, P, HA, HB, p);
 }
 
 void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s) {

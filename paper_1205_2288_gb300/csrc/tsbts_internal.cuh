@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace tsbts {
 
 constexpr int kMaxLevels = 64;
@@ -83,6 +85,14 @@ struct Bodies {
   int* act;          // active list of the step
   int* cursor;       // per body: last previous-pass record with tau <= T
   int* last;         // per body: its last record in the current pass
+  // per body: the previous-pass records bracketing the block time, copied
+  // out of the history so that prediction reads them coalesced. seg_ta is
+  // the time of record A (LLONG_MAX: not loaded), seg_tb that of record B
+  // (-1: A is the body's last record). seg holds 18 arrays of n doubles:
+  // r, v, a of A (components 0..8) and of B (9..17).
+  long long* seg_ta;
+  long long* seg_tb;
+  double* seg;
   double* part;      // force partials [nsplit][5][n_act]
   long long part_cap;  // doubles in part
 };
@@ -106,9 +116,25 @@ struct Params {
   long long lg_cap;
 };
 
+// Work plan of one force launch: IG active bodies per work item (128 / IG
+// threads per body), n_g i-groups, S j-splits of `chunk` j each; direct = 1
+// reads j records straight from global memory instead of staging tiles in
+// shared memory (for narrow groups, where a tile would be reused by few
+// bodies).
+struct Plan {
+  int ig;
+  int n_g;
+  int S;
+  int chunk;
+  int direct;
+};
+
 // Arguments of the force kernels (shared by the integrator and the
 // stand-alone force entry point).
 struct ForceArgs {
+  const Plan* plans;   // plan per active count 0..n (nullable)
+  Plan plan;           // used when has_plan
+  int has_plan;
   int n;
   // FP64 structure-of-arrays j data
   const double* m;
@@ -134,17 +160,29 @@ struct ForceArgs {
 // FP64 step arithmetic, op by op.
 // ---------------------------------------------------------------------
 
+// Largest 2^-k <= x with k_min <= k <= k_max, in ticks (Eq. 4). The
+// largest power of two <= x is 2^e with e the unbiased exponent field of x,
+// so no floating-point arithmetic is needed. x <= 0, NaN and x < 2^-k_max
+// give one tick and set *underflow; x >= 2^-k_min (and +inf) give dt_max.
 __host__ __device__ inline long long level_ticks(double x, int k_min,
                                                  int k_max, int* underflow) {
-  // largest 2^-k <= x with k_min <= k <= k_max, in ticks (Eq. 4)
-  double p = 1.0;
-  for (int k = 0; k < k_min; ++k) p *= 0.5;
-  for (int k = k_min; k <= k_max; ++k) {
-    if (p <= x) return 1LL << (k_max - k);
-    p *= 0.5;
+  if (!(x > 0.0)) {
+    if (underflow) *underflow = 1;
+    return 1;
   }
-  if (underflow) *underflow = 1;
-  return 1;
+#ifdef __CUDA_ARCH__
+  const long long bits = __double_as_longlong(x);
+#else
+  long long bits;
+  __builtin_memcpy(&bits, &x, sizeof bits);
+#endif
+  const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+  if (e >= -k_min) return 1LL << (k_max - k_min);
+  if (-e > k_max) {
+    if (underflow) *underflow = 1;
+    return 1;
+  }
+  return 1LL << (k_max + e);
 }
 
 __host__ __device__ inline int level_of(long long dt_ticks, int k_max) {
@@ -257,6 +295,14 @@ struct ForceLaunch {
 };
 
 ForceLaunch force_launch_shape(int precision, int device);
+Plan plan_force(int precision, int exact, int n_act, int n, int grid,
+                long long part_cap);
+// measured plans of the mixed force kernel per active count 0..n (cached
+// per device, n and grid for the life of the process)
+const std::vector<Plan>* tuned_plans(int device, int n, int grid);
+cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
+                                 const ForceLaunch& fl, int* d_nsplit,
+                                 cudaStream_t s, std::vector<Plan>* table);
 cudaError_t launch_force(int precision, const ForceArgs& fa,
                          const ForceLaunch& fl, cudaStream_t s);
 // sum nsplit partials per active body into AoS a, phi, q

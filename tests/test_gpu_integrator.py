@@ -224,3 +224,21 @@ def test_repeatable_and_deterministic():
         g.close()
     for key in ("r", "v", "a", "tau", "dt"):
         np.testing.assert_array_equal(out[0][key], out[1][key])
+
+
+@pytest.mark.parametrize("graph_steps", [0, 16])
+def test_force_timing_counts_real_steps(orc, graph_steps):
+    """With timing on, every block step's force launch is timed once and
+    the results do not change."""
+    m, r, v = inputs.plummer(512, 29)
+    kw = dict(CFG1, eta=0.03)
+    o = orc.Sim(m, r, v, **kw)
+    o.run(0.25)
+    g = tsbts.Simulation(m, r, v, graph_steps=graph_steps, **kw)
+    g.set_timing(True)
+    g.step_era(0.25)
+    st = g.stats()
+    assert st["force_launches"] == st["block_steps"] == o.stats()["block_steps"]
+    assert st["force_ms"] > 0
+    assert st["kernel_launches"] >= 3 * st["block_steps"]
+    assert_same_state(o, g)
