@@ -133,7 +133,8 @@ void alloc_history(tsbts_ctx* c, int b, long long cap) {
     h.a[d] = dalloc<double>(L, cap);
   }
   h.dts = dalloc<double>(L, cap);
-  h.next = dalloc<int>(L, cap);
+  h.body = dalloc<int>(L, cap);
+  h.seq = dalloc<int>(L, cap);
   h.cap = cap;
   c->graph_dirty = true;
 }
@@ -277,9 +278,9 @@ void check_progress(tsbts_ctx* c, int real, long long pass_steps,
 
 // run one pass; returns the device error bits
 int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
-  History& cur = (pass & 1) ? c->H[1] : c->H[0];
+  // H[0] collects this pass's records; H[1] holds the previous pass's
   launch_pass_begin(c->d_ctl, c->t_sys, tau_e, pass, (int)c->eras, c->n, c->s);
-  launch_pass_setup(c->B, c->P, cur, c->s);
+  launch_pass_setup(c->B, c->P, c->H[0], c->s);
   ck(cudaGetLastError(), "pass set-up");
   c->launches += 2;
   const int G = c->cfg.graph_steps;
@@ -359,6 +360,13 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
         const unsigned long long s0 = c->h_ctl->steps;
         const int e = run_pass(c, p, tau_e, est);
         est = (long long)(c->h_ctl->steps - s0);
+        if (!e && p + 1 < c->cfg.n_iter) {
+          // the next pass interpolates from these records, body-major
+          launch_history_to_csr(c->B, c->H[0], c->H[1], c->d_ctl, c->sms,
+                                c->s);
+          ck(cudaGetLastError(), "history reorder");
+          c->launches += 4;
+        }
         if (e & kErrHistory) {
           grow = true;
           break;
@@ -373,8 +381,13 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
                           std::to_string(e) + ")");
       }
       if (!grow) break;
-      // the history did not fit: grow both buffers, re-run the era
-      const long long cap = std::max(c->H[0].cap * 4, c->max_rec * 2);
+      // the history did not fit: grow both buffers, re-run the era (record
+      // indices are 32-bit)
+      const long long cap = std::min<long long>(
+          std::max(c->H[0].cap * 4, c->max_rec * 2), 0x7fffffffLL);
+      if (c->max_rec >= cap)
+        return fail(c, TSBTS_ERR_HISTORY,
+                    "era history exceeds 2^31 records; use a shorter era");
       ck(cudaStreamSynchronize(c->s), "synchronize");
       alloc_history(c, 0, cap);
       alloc_history(c, 1, cap);
@@ -412,7 +425,11 @@ void setup_bodies(tsbts_ctx* c, int n) {
   B.jv = dalloc<float4>(L, n);
   B.act = dalloc<int>(L, n);
   B.cursor = dalloc<int>(L, n);
-  B.last = dalloc<int>(L, n);
+  B.hcnt = dalloc<int>(L, n);
+  B.hoff = dalloc<int>(L, (size_t)n + 1);
+  B.scan_tmp = dalloc<int>(L, (size_t)(n + 1023) / 1024);
+  ck(cudaMemsetAsync(B.hoff, 0, sizeof(int) * ((size_t)n + 1), c->s),
+     "memset");
   B.seg_ta = dalloc<long long>(L, n);
   B.seg_tb = dalloc<long long>(L, n);
   B.seg = dalloc<double>(L, 18 * (size_t)n);

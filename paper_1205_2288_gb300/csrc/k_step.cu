@@ -54,9 +54,10 @@ __global__ void pass_setup_kernel(Bodies B, Params P, History cur) {
       cur.a[c][i] = B.a[c][i];
     }
     cur.dts[i] = B.dts[i];
-    cur.next[i] = -1;
-    B.last[i] = i;
-    B.cursor[i] = i;
+    cur.body[i] = i;
+    cur.seq[i] = 0;
+    B.hcnt[i] = 1;
+    B.cursor[i] = B.hoff[i];  // first previous-pass record of body i
     B.seg_ta[i] = LLONG_MAX;
     atomicAdd(&h[level_of(B.dt[i], P.k_max)], 1);
   }
@@ -127,7 +128,7 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
   const long long tn = s_tn;
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->slot[p].tau_next = tn;
   const int pass = ctl->pass;
-  const History& prev = (pass & 1) ? HA : HB;
+  const History& prev = HB;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = false;
   if (j < B.n) {
@@ -139,19 +140,16 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
     bool have = false;
     if (pass > 0 && !act) {
       // previous-pass records A <= tn < B of body j, from the segment cache;
-      // refilled from the history chain only when tn leaves the segment
+      // refilled from the body's contiguous records when tn leaves it
       const int n = B.n;
       long long ta = B.seg_ta[j], tb = B.seg_tb[j];
       if (!(ta <= tn && (tb < 0 || tn < tb))) {
         int c = B.cursor[j];
+        const int end = B.hoff[j + 1];
         if (prev.tau[c] <= tn) {
-          for (;;) {
-            const int nx = prev.next[c];
-            if (nx < 0 || prev.tau[nx] > tn) break;
-            c = nx;
-          }
+          while (c + 1 < end && prev.tau[c + 1] <= tn) ++c;
           B.cursor[j] = c;
-          const int nx = prev.next[c];
+          const int nx = c + 1 < end ? c + 1 : -1;
           ta = prev.tau[c];
           tb = nx >= 0 ? prev.tau[nx] : -1;
           for (int d = 0; d < 3; ++d) {
@@ -220,8 +218,8 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
   const long long tn = sl.tau_next;
   const int S = sl.nsplit;
   const int pass = ctl->pass;
-  const History& cur = (pass & 1) ? HB : HA;
-  const History& prev = (pass & 1) ? HA : HB;
+  const History& cur = HA;
+  const History& prev = HB;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act;
        k += gridDim.x * blockDim.x) {
     const int i = B.act[k];
@@ -270,9 +268,10 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
         cur.a[c][rec] = an[c];
       }
       cur.dts[rec] = dts;
-      cur.next[rec] = -1;
-      cur.next[B.last[i]] = (int)rec;
-      B.last[i] = (int)rec;
+      cur.body[rec] = i;
+      const int sq = B.hcnt[i];
+      cur.seq[rec] = sq;
+      B.hcnt[i] = sq + 1;
     } else {
       atomicOr(&ctl->err, kErrHistory);
     }
@@ -281,19 +280,16 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
     if (pass == 0) {
       c = forward_step(tn, d, dts, P.k_min, P.k_max, &uf);
     } else {
-      // advance the body's previous-pass cursor to the block time so that
-      // the lookups below walk only the records of this step
+      // advance the body's previous-pass cursor to the block time; the
+      // lookups below then read the few records that follow it
       int start = B.cursor[i];
+      const int end = B.hoff[i + 1];
       if (prev.tau[start] <= tn) {
-        for (;;) {
-          const int nx = prev.next[start];
-          if (nx < 0 || prev.tau[nx] > tn) break;
-          start = nx;
-        }
+        while (start + 1 < end && prev.tau[start + 1] <= tn) ++start;
         B.cursor[i] = start;
       }
-      const double e2 = history_dts_at(prev, start, tn + 2 * d, dts);
-      const double e1 = history_dts_at(prev, start, tn + d, dts);
+      const double e2 = history_dts_at(prev, start, end, tn + 2 * d, dts);
+      const double e1 = history_dts_at(prev, start, end, tn + d, dts);
       c = symmetric_step(tn, d, dts, e2, e1, P.k_min, P.k_max, P.dtmax_t,
                          &uf);
     }
@@ -344,6 +340,100 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
 // ---------------------------------------------------------------------
 // Era helpers: snapshot/restore, next-time extrema (Alg. 3)
 // ---------------------------------------------------------------------
+// ---------------------------------------------------------------------
+// Between passes: the running pass's appended records become the next
+// pass's previous-pass records in body-major (CSR) order. hoff is the
+// exclusive scan of the per-body record counts; each record then moves to
+// hoff[body] + rank.
+// ---------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 4;
+constexpr int kScanBlock = kScanThreads * kScanPer;
+
+// block-wide inclusive scan of one value per thread (kScanThreads threads)
+__device__ __forceinline__ int block_inclusive_scan(int x, int* warp_tot) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kScanThreads / 32) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  return wid ? x + warp_tot[wid - 1] : x;
+}
+
+__global__ void scan_block_sums_kernel(const int* cnt, int n, int* bsum) {
+  __shared__ int wt[kScanThreads / 32];
+  const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+  int s = 0;
+  for (int e = 0; e < kScanPer; ++e)
+    if (base + e < n) s += cnt[base + e];
+  const int inc = block_inclusive_scan(s, wt);
+  if (threadIdx.x == kScanThreads - 1) bsum[blockIdx.x] = inc;
+}
+
+// exclusive scan of the block sums in place, one block
+__global__ void scan_bsum_kernel(int* bsum, int nblk) {
+  __shared__ int wt[kScanThreads / 32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblk; b0 += kScanThreads) {
+    const int b = b0 + threadIdx.x;
+    const int x = b < nblk ? bsum[b] : 0;
+    const int inc = block_inclusive_scan(x, wt);
+    const int c = carry;
+    if (b < nblk) bsum[b] = c + inc - x;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = c + inc;
+    __syncthreads();
+  }
+}
+
+__global__ void scan_write_kernel(const int* cnt, int n, const int* bsum,
+                                  int* off) {
+  __shared__ int wt[kScanThreads / 32];
+  const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+  int v[kScanPer], s = 0;
+  for (int e = 0; e < kScanPer; ++e) {
+    v[e] = base + e < n ? cnt[base + e] : 0;
+    s += v[e];
+  }
+  int run = block_inclusive_scan(s, wt) - s + bsum[blockIdx.x];
+  for (int e = 0; e < kScanPer; ++e) {
+    run += v[e];
+    if (base + e < n) off[base + e + 1] = run;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) off[0] = 0;
+}
+
+__global__ void history_scatter_kernel(History src, History dst,
+                                       const int* off, const Ctl* ctl) {
+  long long nrec = ctl->slot[0].nrec > ctl->slot[1].nrec ? ctl->slot[0].nrec
+                                                         : ctl->slot[1].nrec;
+  if (nrec > src.cap) nrec = src.cap;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       r < nrec; r += (long long)gridDim.x * blockDim.x) {
+    const long long d = (long long)off[src.body[r]] + src.seq[r];
+    dst.tau[d] = src.tau[r];
+    for (int c = 0; c < 3; ++c) {
+      dst.r[c][d] = src.r[c][r];
+      dst.v[c][d] = src.v[c][r];
+      dst.a[c][d] = src.a[c][r];
+    }
+    dst.dts[d] = src.dts[r];
+  }
+}
+
 __global__ void copy_state_kernel(Bodies dst, Bodies src) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dst.n;
        i += gridDim.x * blockDim.x) {
@@ -529,6 +619,18 @@ void launch_pass_begin(Ctl* ctl, long long tau_s, long long tau_e, int pass,
   pass_begin_kernel<<<1, kMaxLevels, 0, s>>>(ctl, tau_s, tau_e, pass, era, n);
 }
 
+void launch_history_to_csr(const Bodies& B, const History& append,
+                           const History& csr, const Ctl* ctl, int sms,
+                           cudaStream_t s) {
+  const int nblk = (B.n + kScanBlock - 1) / kScanBlock;
+  scan_block_sums_kernel<<<nblk, kScanThreads, 0, s>>>(B.hcnt, B.n,
+                                                       B.scan_tmp);
+  scan_bsum_kernel<<<1, kScanThreads, 0, s>>>(B.scan_tmp, nblk);
+  scan_write_kernel<<<nblk, kScanThreads, 0, s>>>(B.hcnt, B.n, B.scan_tmp,
+                                                  B.hoff);
+  history_scatter_kernel<<<sms * 8, 256, 0, s>>>(append, csr, B.hoff, ctl);
+}
+
 void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
                        cudaStream_t s) {
   pass_setup_kernel<<<grid_for(B.n, 256, 2048), 256, 0, s>>>(B, P, cur);
@@ -536,8 +638,9 @@ void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
 
 void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
                            const History& HB, int p, cudaStream_t s) {
-  select_predict_kernel<<<grid_for(B.n, 128, 1 << 30), 128, 0, s>>>(B, P, HA, HB,
-                                                                  p);
+  // 64-thread blocks spread the FP64 prediction over more SMs
+  select_predict_kernel<<<grid_for(B.n, 64, 1 << 30), 64, 0, s>>>(B, P, HA,
+                                                                  HB, p);
 }
 
 void launch_correct(const Bodies& B, const Params& P, const History& HA,

@@ -24,16 +24,22 @@ constexpr int kErrInvariant = 4;  // block-time invariant broken (bug)
 constexpr int kErrLevels = 8;     // level histogram empty (bug)
 
 // One pass's era history (Sec. 2: the state of every body at each of its
-// steps within the era). Records 0..n-1 are the era-start records of the
-// bodies; later records are appended in block-step order and chained per
-// body through `next` (-1 ends a chain).
+// steps within the era). Two buffers with fixed roles:
+//  - the append buffer of the running pass: records 0..n-1 are the bodies'
+//    era-start records, later ones are appended in block-step order, each
+//    tagged with its body and its rank among that body's records;
+//  - the previous pass's records in body-major order (CSR): body b owns
+//    records hoff[b] .. hoff[b+1]-1 in time order, so a body's records are
+//    contiguous and walking them reads consecutive memory.
+// Between two passes the append buffer is scattered into CSR order.
 struct History {
   long long* tau;
   double* r[3];
   double* v[3];
   double* a[3];
   double* dts;
-  int* next;
+  int* body;  // append buffer only
+  int* seq;   // append buffer only
   long long cap;
 };
 
@@ -83,8 +89,11 @@ struct Bodies {
   float4* jlo;
   float4* jv;
   int* act;          // active list of the step
-  int* cursor;       // per body: last previous-pass record with tau <= T
-  int* last;         // per body: its last record in the current pass
+  int* cursor;       // per body: its last previous-pass record (CSR index)
+                     // with tau <= the current block time
+  int* hcnt;         // per body: records appended in the running pass
+  int* hoff;         // n + 1 CSR offsets of the previous pass's records
+  int* scan_tmp;     // block sums of the offset scan
   // per body: the previous-pass records bracketing the block time, copied
   // out of the history so that prediction reads them coalesced. seg_ta is
   // the time of record A (LLONG_MAX: not loaded), seg_tb that of record B
@@ -265,21 +274,19 @@ __device__ inline double hermite1(const HermiteW& w, double ya, double da,
 
 // previous pass's step estimate of a body at tick t (linear between the
 // bracketing records; fallback past the stored records)
-__device__ inline double history_dts_at(const History& H, int start,
+// Previous pass's step estimate of a body at tick t, from its CSR records
+// [start, end) (start has tau <= the current block time <= t): linear
+// between the bracketing records, `fallback` past the last record.
+__device__ inline double history_dts_at(const History& H, int start, int end,
                                         long long t, double fallback) {
   int c = start;
   if (H.tau[c] > t) return fallback;
-  for (;;) {
-    const int nx = H.next[c];
-    if (nx < 0 || H.tau[nx] > t) break;
-    c = nx;
-  }
+  while (c + 1 < end && H.tau[c + 1] <= t) ++c;
   if (H.tau[c] == t) return H.dts[c];
-  const int nx = H.next[c];
-  if (nx < 0) return fallback;
+  if (c + 1 >= end) return fallback;
   const double w = __ddiv_rn((double)(t - H.tau[c]),
-                             (double)(H.tau[nx] - H.tau[c]));
-  return __dadd_rn(H.dts[c], __dmul_rn(__dsub_rn(H.dts[nx], H.dts[c]), w));
+                             (double)(H.tau[c + 1] - H.tau[c]));
+  return __dadd_rn(H.dts[c], __dmul_rn(__dsub_rn(H.dts[c + 1], H.dts[c]), w));
 }
 
 // ---------------------------------------------------------------------

@@ -16,6 +16,10 @@ void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
 void launch_correct(const Bodies& B, const Params& P, const History& HA,
                     const History& HB, int p, int grid, cudaStream_t s);
 void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s);
+// the running pass's appended records -> previous-pass records in CSR order
+void launch_history_to_csr(const Bodies& B, const History& append,
+                           const History& csr, const Ctl* ctl, int sms,
+                           cudaStream_t s);
 void launch_next_time_extrema(const Bodies& B, Ctl* ctl, cudaStream_t s);
 void launch_load_aos(const Bodies& B, const double* m, const double* r,
                      const double* v, Ctl* ctl, cudaStream_t s);
