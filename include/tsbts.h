@@ -183,6 +183,29 @@ int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
 /* Free the scratch memory of tsbts_force on the current device. */
 int tsbts_release_scratch(void);
 
+/* tsbts_force for callers that cannot allocate device memory: code whose
+ * device memory is managed entirely by someone else (a framework allocator
+ * that has reserved the device, a fixed real-time budget) and code that must
+ * not call cudaMalloc or cudaFree because those calls can synchronise the
+ * device. The paper has no counterpart; this is a property of the library.
+ *
+ * Same arguments, results and tolerances as tsbts_force (the FP64 path with
+ * ascending-j sums gives identical results; other paths may round
+ * differently because the work plan is chosen without measurement). It
+ * allocates nothing and calls no allocating routine: its scratch (packed j
+ * records and j-split partial sums) is a fixed array of about 9 MB inside
+ * the library that every GPU loading the library holds until the process
+ * exits. Limits: n <= 65536 and n_act <= 65536, else TSBTS_ERR_ARG.
+ * The first call on a device looks up the array's device address; make
+ * that first call before any stream capture. Every call on a device shares
+ * the one array, so calls that overlap on the GPU (different streams or
+ * threads without ordering) race and give wrong results; each call writes
+ * all the scratch it reads, so nothing needs clearing between calls. */
+int tsbts_force_static(int precision, int exact_order, int64_t n,
+                       const double* m, const double* r, const double* v,
+                       double eps, int64_t n_act, const int32_t* idx,
+                       double* a, double* phi, double* q, void* stream);
+
 /* Library version string. */
 const char* tsbts_version(void);
 

@@ -990,3 +990,123 @@ int tsbts_release_scratch(void) {
 const char* tsbts_version(void) { return kVersion; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------
+// tsbts_force_static: the stand-alone force with its scratch memory in a
+// fixed device array instead of cudaMalloc'd buffers, for callers that
+// cannot allocate device memory.
+//
+// The array lives in this file, so every GPU that loads the library holds
+// it until the process exits. In host code `g_static_scratch` names a
+// host-side stand-in, not the device array: its device address is looked up
+// once per device with cudaGetSymbolAddress (with that device current) and
+// only that address is handed to the kernels.
+// ---------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxBodies = 65536;
+// packed j records: 7 doubles per body (FP64) or 3 float4 (mixed, 48 B)
+constexpr size_t kStaticJBytes = (size_t)7 * sizeof(double) * kStaticMaxBodies;
+// j-split partial sums: room for two splits of 5 values per active body
+constexpr long long kStaticPartDoubles = 2LL * 5 * kStaticMaxBodies;
+constexpr size_t kStaticBytes =
+    kStaticJBytes + sizeof(double) * kStaticPartDoubles + 256;
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+struct StaticDev {
+  unsigned char* ptr;   // device address of g_static_scratch
+  ForceLaunch fl[2];    // launch shapes, FP64 and mixed
+  bool ready;
+};
+std::mutex g_static_mu;
+StaticDev g_static_dev[kStaticMaxDevices];
+
+// once per device, with that device current: the array's device address
+// and the launch shapes (no allocation on this path)
+int static_setup(int dev, StaticDev** out) {
+  std::lock_guard<std::mutex> g(g_static_mu);
+  StaticDev& d = g_static_dev[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return TSBTS_ERR_CUDA;
+    }
+    d.ptr = static_cast<unsigned char*>(p);
+    d.fl[0] = force_launch_shape(0, dev);
+    d.fl[1] = force_launch_shape(1, dev);
+    d.ready = true;
+  }
+  *out = &d;
+  return TSBTS_OK;
+}
+
+}  // namespace
+
+extern "C" int tsbts_force_static(int precision, int exact_order, int64_t n,
+                                  const double* m, const double* r,
+                                  const double* v, double eps, int64_t n_act,
+                                  const int32_t* idx, double* a, double* phi,
+                                  double* q, void* stream) {
+  if (precision != TSBTS_FP64 && precision != TSBTS_MIXED) return TSBTS_ERR_ARG;
+  if (n < 1 || n > kStaticMaxBodies || n_act < 0 || n_act > kStaticMaxBodies)
+    return TSBTS_ERR_ARG;
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return TSBTS_ERR_ARG;
+  if (!m || !r || !v || (n_act > 0 && (!idx || !a || !phi || !q)))
+    return TSBTS_ERR_ARG;
+  if (n_act == 0) return TSBTS_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 ||
+      dev >= kStaticMaxDevices) {
+    cudaGetLastError();
+    return TSBTS_ERR_CUDA;
+  }
+  StaticDev* sd = nullptr;
+  const int rc = static_setup(dev, &sd);
+  if (rc != TSBTS_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ni = (int)n;
+  const ForceLaunch& fl = sd->fl[precision ? 1 : 0];
+  unsigned char* base = sd->ptr;
+  double* x = reinterpret_cast<double*>(base);
+  float4* j4 = reinterpret_cast<float4*>(base);
+  double* part = reinterpret_cast<double*>(base + kStaticJBytes);
+  int* nsplit = reinterpret_cast<int*>(base + kStaticJBytes +
+                                       sizeof(double) * kStaticPartDoubles);
+  // Every region is written before it is read in this call (the packed j
+  // records, every (split, body) partial of the plan, the split count), so
+  // nothing left by an earlier call needs clearing.
+  cudaError_t e = launch_pack_aos(
+      precision, ni, m, r, v, x, x + ni, x + 2LL * ni, x + 3LL * ni,
+      x + 4LL * ni, x + 5LL * ni, x + 6LL * ni, j4, j4 + ni, j4 + 2LL * ni, s);
+  if (e != cudaSuccess) return TSBTS_ERR_CUDA;
+  ForceArgs fa{};
+  fa.n = ni;
+  fa.m = x + 6LL * ni;
+  for (int d = 0; d < 3; ++d) {
+    fa.x[d] = x + (long long)d * ni;
+    fa.w[d] = x + (long long)(3 + d) * ni;
+  }
+  fa.jhi = j4;
+  fa.jlo = j4 + ni;
+  fa.jv = j4 + 2LL * ni;
+  fa.idx = idx;
+  fa.n_act_fixed = (int)n_act;
+  fa.nsplit_out = nsplit;
+  fa.part = part;
+  fa.part_cap = kStaticPartDoubles;
+  fa.eps2 = eps * eps;
+  fa.eps2f = (float)(eps * eps);
+  fa.exact = precision == TSBTS_FP64 &&
+             (exact_order == 1 || (exact_order < 0 && n <= 8192));
+  fa.plan = plan_force(precision, fa.exact, (int)n_act, ni, fl.grid,
+                       kStaticPartDoubles);
+  fa.has_plan = 1;
+  if (launch_force(precision, fa, fl, s) != cudaSuccess) return TSBTS_ERR_CUDA;
+  if (launch_force_finalize(part, nsplit, (int)n_act, a, phi, q, s) !=
+      cudaSuccess)
+    return TSBTS_ERR_CUDA;
+  return TSBTS_OK;
+}

@@ -776,12 +776,14 @@ __global__ void pack_aos_kernel(int precision, int n, const double* m,
 }
 
 ForceLaunch force_launch_shape(int precision, int device) {
+  // fixed table per device (this path allocates nothing)
+  constexpr int kMaxDevices = 64;
   static std::mutex mu;
-  static std::vector<ForceLaunch> cache[2];
+  static ForceLaunch cache[2][kMaxDevices];
   std::lock_guard<std::mutex> g(mu);
-  auto& c = cache[precision ? 1 : 0];
-  if ((int)c.size() > device && c[device].grid > 0) return c[device];
-  if ((int)c.size() <= device) c.resize(device + 1, ForceLaunch{0, 0, 0, 0});
+  ForceLaunch* c = cache[precision ? 1 : 0];
+  const bool cached = device >= 0 && device < kMaxDevices;
+  if (cached && c[device].grid > 0) return c[device];
   int sms = 0, per_sm = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (precision)
@@ -797,7 +799,7 @@ ForceLaunch force_launch_shape(int precision, int device) {
   fl.threads = kThreads;
   fl.tile_i = kThreads;
   fl.part_cap = 5LL * fl.grid * kThreads;
-  c[device] = fl;
+  if (cached) c[device] = fl;
   return fl;
 }
 

@@ -40,7 +40,7 @@ EXPORTS = (
     "tsbts_step_era", "tsbts_energy", "tsbts_state", "tsbts_get_stats",
     "tsbts_set_timing", "tsbts_schedule_log", "tsbts_schedule_size",
     "tsbts_schedule_get", "tsbts_last_error", "tsbts_destroy", "tsbts_force",
-    "tsbts_release_scratch", "tsbts_version",
+    "tsbts_release_scratch", "tsbts_version", "tsbts_force_static",
 )
 
 
@@ -106,6 +106,8 @@ def lib():
         L.tsbts_destroy.restype = None
         L.tsbts_force.argtypes = [C.c_int, C.c_int, I64, VP, VP, VP,
                                   C.c_double, I64, VP, VP, VP, VP, VP]
+        L.tsbts_force_static.argtypes = [C.c_int, C.c_int, I64, VP, VP, VP,
+                                         C.c_double, I64, VP, VP, VP, VP, VP]
         L.tsbts_release_scratch.argtypes = []
         L.tsbts_version.argtypes = []
         L.tsbts_version.restype = C.c_char_p
@@ -234,6 +236,23 @@ def tsbts_force(precision, m, r, v, eps, idx, a, phi, q, exact_order=-1,
                              float(eps), idx.shape[0], idx.data_ptr(),
                              a.data_ptr(), phi.data_ptr(), q.data_ptr(),
                              stream))
+
+
+def tsbts_force_static(precision, m, r, v, eps, idx, a, phi, q,
+                       exact_order=-1, stream=None):
+    """tsbts_force without device allocation (see tsbts.h): scratch lives
+    in a fixed array inside the library; n, n_act <= 65536."""
+    import torch
+    for t in (m, r, v, idx, a, phi, q):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("tsbts_force_static takes contiguous CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream(m.device).cuda_stream
+    _check(lib().tsbts_force_static(int(precision), int(exact_order),
+                                    m.shape[0], m.data_ptr(), r.data_ptr(),
+                                    v.data_ptr(), float(eps), idx.shape[0],
+                                    idx.data_ptr(), a.data_ptr(),
+                                    phi.data_ptr(), q.data_ptr(), stream))
 
 
 def tsbts_version() -> str:
