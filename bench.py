@@ -261,6 +261,70 @@ def force_sweep(args):
     return 0
 
 
+def ensemble_bench(args):
+    """512 independent Plummer clusters (sizes log-uniform in [64, 4096],
+    Salpeter masses, eps = 4/N_c) integrated together over t = 0..0.5,
+    mixed precision, fixed era 1/8, three passes."""
+    import torch
+
+    from paper_1205_2288_gb300 import inputs, tsbts
+
+    off, m, r, v, eps = inputs.ensemble(args.clusters, seed=SEED)
+    t_end = args.t_end if args.t_end != T_END else 0.5
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(eps=eps, eta=ETA, dt_max=DT_MAX, precision=tsbts.TSBTS_MIXED,
+              n_iter=N_ITER, era_log2=3, stream=stream.cuda_stream)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    tot_s = 0.0
+    tot_i = tot_steps = tot_launch = 0
+    force_ms = 0.0
+    force_n = 0
+    for it in range(args.warmup + args.steps):
+        g = tsbts.Ensemble(off, m, r, v, **kw)
+        g.set_timing(it >= args.warmup)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step_era(t_end)
+        e1.record(stream)
+        e1.synchronize()
+        st = g.stats()
+        if it >= args.warmup:
+            tot_s += e0.elapsed_time(e1) / 1e3
+            tot_i += st["interactions"]
+            tot_steps += st["block_steps"]
+            tot_launch += st["kernel_launches"]
+            force_ms += st["force_ms"]
+            force_n += st["force_launches"]
+        g.close()
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2070e6 / OPS_PER_INTERACTION
+    achieved = tot_i / (force_ms / 1e3) if force_ms else 0.0
+    line = {
+        "metric": "ensemble G pair-interactions/s (512 Plummer clusters)",
+        "value": tot_i / tot_s / 1e9, "unit": "Ginteractions/s",
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_s / args.steps,
+        "config": {"workload": f"ensemble{args.clusters}_plummer_salpeter_"
+                               f"n64-4096_eps4overN_t0-{t_end}",
+                   "clusters": args.clusters, "bodies": int(off[-1]),
+                   "eta": ETA, "dt_max": DT_MAX, "era": "fixed 1/8",
+                   "n_iter": N_ITER, "precision": "mixed"},
+        "global_block_steps_per_s": tot_steps / tot_s,
+        "kernel_launches_per_global_step": 5,
+        "gpu_launches": tot_launch,
+        "interactions_per_step": tot_i / args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9,
+                     "peak": peak / 1e9, "unit": "Ginteractions/s",
+                     "frac": achieved / peak, "kernel": "ens_force_mixed_kernel",
+                     "force_launches": force_n},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,9 +338,14 @@ def main():
                     help="time the force kernel alone on n = 131072")
     ap.add_argument("--n-act", default="",
                     help="comma-separated active-set sizes for --force-sweep")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="integrate the 512-cluster ensemble instead")
+    ap.add_argument("--clusters", type=int, default=512)
     args = ap.parse_args()
     if args.force_sweep:
         return force_sweep(args)
+    if args.ensemble:
+        return ensemble_bench(args)
     ws, rank, local = dist_env()
     dist = init_dist(ws)
     if args.impl == "reference":

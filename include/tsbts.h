@@ -112,6 +112,25 @@ int tsbts_init_device(tsbts_ctx* ctx, int64_t n, const double* m_dev,
                       const double* r_dev, const double* v_dev, double eps,
                       double eta, double dt_max);
 
+/* Alg. 2 step 1 for an ensemble of independent clusters integrated
+ * together (the batched form of the method; each cluster is its own
+ * N-body system with its own block times and its own softening). Cluster
+ * c owns bodies offsets[c] .. offsets[c+1]-1 of the HOST arrays m[n],
+ * r[n*3], v[n*3] (n = offsets[n_clusters], offsets[0] = 0, every cluster
+ * non-empty, 1 <= n_clusters <= 4096); eps[n_clusters] its softening
+ * lengths. eta and dt_max as in tsbts_init. The context must use a fixed
+ * era (era_mode 0). Afterwards tsbts_step_era advances every cluster over
+ * the same eras; tsbts_state returns all bodies; tsbts_energy returns the
+ * sums over the clusters; the schedule log is not recorded. */
+int tsbts_init_ensemble(tsbts_ctx* ctx, int64_t n_clusters,
+                        const int64_t* offsets, const double* m,
+                        const double* r, const double* v, const double* eps,
+                        double eta, double dt_max);
+
+/* Per-cluster kinetic and potential energy of an ensemble at the system
+ * time (HOST arrays of n_clusters doubles, each may be NULL). */
+int tsbts_ensemble_energy(tsbts_ctx* ctx, double* ekin, double* epot);
+
 /* Alg. 2 steps 2-11 (Alg. 3 for the dynamic era): integrate whole eras,
  * each with n_iter passes, until the system time reaches t_end. t_end must
  * be a whole number of ticks and not before the system time

@@ -81,7 +81,23 @@ struct tsbts_ctx {
   // CUDA graph of graph_steps block steps
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
+  // ensemble of independent clusters (tsbts_init_ensemble)
+  bool ensemble = false;
+  int nc = 0;
+  Ens E{};
+  ForceLaunch efl{};
+  double* d_ek = nullptr;
+  double* d_ep = nullptr;
 };
+
+namespace {
+// clusters of tsbts_init_ensemble, host arrays
+struct EnsInput {
+  int64_t nc;
+  const int64_t* offsets;  // nc + 1
+  const double* eps;       // nc
+};
+}  // namespace
 
 namespace {
 
@@ -216,6 +232,14 @@ void enqueue_step(tsbts_ctx* c, int p, int ev_slot, bool capturing) {
   const History& HB = c->H[1];
   const unsigned evflags =
       capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (c->ensemble) {
+    launch_ens_step(c->B, c->P, c->E, HA, HB, c->efl, c->cfg.precision,
+                    c->exact, ev_slot >= 0 ? c->ev[2 * ev_slot] : nullptr,
+                    ev_slot >= 0 ? c->ev[2 * ev_slot + 1] : nullptr, evflags,
+                    c->s);
+    ck(cudaGetLastError(), "ensemble step launch");
+    return;
+  }
   launch_select_predict(c->B, c->P, HA, HB, p, c->s);
   if (ev_slot >= 0)
     ck(cudaEventRecordWithFlags(c->ev[2 * ev_slot], c->s, evflags), "event");
@@ -280,9 +304,16 @@ void check_progress(tsbts_ctx* c, int real, long long pass_steps,
 int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
   // H[0] collects this pass's records; H[1] holds the previous pass's
   launch_pass_begin(c->d_ctl, c->t_sys, tau_e, pass, (int)c->eras, c->n, c->s);
-  launch_pass_setup(c->B, c->P, c->H[0], c->s);
+  if (c->ensemble) {
+    launch_ens_pass_begin(c->E, c->t_sys, c->s);
+    launch_ens_pass_setup(c->B, c->P, c->E, c->H[0], c->s);
+    c->launches += 3;
+  } else {
+    launch_pass_setup(c->B, c->P, c->H[0], c->s);
+    c->launches += 2;
+  }
   ck(cudaGetLastError(), "pass set-up");
-  c->launches += 2;
+  const int per_step = c->ensemble ? 5 : 3;  // kernels per block step
   const int G = c->cfg.graph_steps;
   unsigned long long steps0 = c->h_ctl->steps;
   long long pass_steps = 0;
@@ -290,7 +321,7 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
     if (c->graph_dirty || !c->gexec) build_graph(c);
     for (;;) {
       ck(cudaGraphLaunch(c->gexec, c->s), "graph launch");
-      c->launches += 3LL * G;
+      c->launches += (long long)per_step * G;
       read_ctl(c);
       const int real = (int)(c->h_ctl->steps - steps0);
       steps0 = c->h_ctl->steps;
@@ -306,7 +337,7 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
       if (c->timing) ensure_events(c, (int)chunk);
       for (long long k = 0; k < chunk; ++k) {
         enqueue_step(c, p, c->timing ? (int)k : -1, false);
-        c->launches += 3;
+        c->launches += per_step;
         p ^= 1;
       }
       read_ctl(c);
@@ -349,6 +380,13 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
     const long long tau_e = std::min(c->t_sys + era_ticks(c), tau_end);
     launch_copy_state(c->snap, c->B, c->s);
     c->launches += 1;
+    // counters at the era start: an era re-run after the history grew
+    // counts (and logs) only the run that is kept
+    read_ctl(c);
+    const Ctl saved = *c->h_ctl;
+    const long long saved_passes = c->passes;
+    const double saved_force_ms = c->force_ms;
+    const long long saved_force_n = c->force_launches;
     for (;;) {
       bool grow = false;
       long long est = 0;
@@ -394,6 +432,18 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
       int zero = 0;
       ck(cudaMemcpyAsync(&c->d_ctl->err, &zero, sizeof zero,
                          cudaMemcpyHostToDevice, c->s), "clear error");
+      // steps, interactions, underflows, then the log counters
+      ck(cudaMemcpyAsync(&c->d_ctl->steps, &saved.steps,
+                         3 * sizeof(unsigned long long),
+                         cudaMemcpyHostToDevice, c->s), "roll back counters");
+      ck(cudaMemcpyAsync(&c->d_ctl->log_steps, &saved.log_steps,
+                         3 * sizeof(long long), cudaMemcpyHostToDevice, c->s),
+         "roll back counters");
+      ck(cudaStreamSynchronize(c->s), "synchronize");
+      *c->h_ctl = saved;
+      c->passes = saved_passes;
+      c->force_ms = saved_force_ms;
+      c->force_launches = saved_force_n;
       launch_copy_state(c->B, c->snap, c->s);
       c->launches += 1;
       c->restarts += 1;
@@ -458,9 +508,60 @@ void setup_bodies(tsbts_ctx* c, int n) {
   alloc_history(c, 1, cap);
 }
 
+// device arrays of an ensemble: body offsets, cluster of each body, per-
+// cluster softening, block-step state and work-list prefixes
+void setup_ensemble(tsbts_ctx* c, const EnsInput& in) {
+  const int nc = (int)in.nc, n = c->n;
+  auto& L = c->allocs;
+  std::vector<int> off(nc + 1), cl(n);
+  std::vector<double> e2(nc);
+  std::vector<float> e2f(nc);
+  for (int k = 0; k <= nc; ++k) off[k] = (int)in.offsets[k];
+  for (int k = 0; k < nc; ++k) {
+    for (int i = off[k]; i < off[k + 1]; ++i) cl[i] = k;
+    e2[k] = in.eps[k] * in.eps[k];
+    e2f[k] = (float)e2[k];
+  }
+  Ens& E = c->E;
+  E = Ens{};
+  E.nc = nc;
+  int* d_off = dalloc<int>(L, nc + 1);
+  int* d_cl = dalloc<int>(L, n);
+  double* d_e2 = dalloc<double>(L, nc);
+  float* d_e2f = dalloc<float>(L, nc);
+  ck(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (nc + 1),
+                     cudaMemcpyHostToDevice, c->s), "copy offsets");
+  ck(cudaMemcpyAsync(d_cl, cl.data(), sizeof(int) * n,
+                     cudaMemcpyHostToDevice, c->s), "copy clusters");
+  ck(cudaMemcpyAsync(d_e2, e2.data(), sizeof(double) * nc,
+                     cudaMemcpyHostToDevice, c->s), "copy eps");
+  ck(cudaMemcpyAsync(d_e2f, e2f.data(), sizeof(float) * nc,
+                     cudaMemcpyHostToDevice, c->s), "copy eps");
+  E.off = d_off;
+  E.cl = d_cl;
+  E.eps2 = d_e2;
+  E.eps2f = d_e2f;
+  E.tau_c = dalloc<long long>(L, nc);
+  E.tau_next = dalloc<long long>(L, nc);
+  E.cnt = dalloc<int>(L, nc);
+  E.hist = dalloc<int>(L, (size_t)nc * kMaxLevels);
+  E.act = dalloc<int>(L, n);
+  E.plan = dalloc<Plan>(L, nc);
+  E.item_off = dalloc<int>(L, nc + 1);
+  E.act_base = dalloc<int>(L, nc + 1);
+  E.part_off = dalloc<long long>(L, nc + 1);
+  E.totals = dalloc<int>(L, 4);
+  ck(cudaMemsetAsync(E.totals, 0, sizeof(int) * 4, c->s), "memset");
+  c->d_ek = dalloc<double>(L, nc);
+  c->d_ep = dalloc<double>(L, nc);
+  c->efl = ens_force_launch_shape(c->cfg.precision, c->cfg.device);
+  c->nc = nc;
+  c->ensemble = true;
+}
+
 int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
                 const double* v, double eps, double eta, double dt_max,
-                bool host) {
+                bool host, const EnsInput* ens = nullptr) {
   if (!c) return TSBTS_ERR_ARG;
   if (c->poisoned) return fail(c, TSBTS_ERR_STATE, "context is poisoned");
   if (n < 1 || n > (1LL << 24))
@@ -468,6 +569,21 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
   if (!m || !r || !v) return fail(c, TSBTS_ERR_ARG, "null input pointer");
   if (!(eps >= 0.0) || !std::isfinite(eps))
     return fail(c, TSBTS_ERR_ARG, "eps must be finite and >= 0");
+  if (ens) {
+    if (ens->nc < 1 || ens->nc > ens_max_clusters() || !ens->offsets ||
+        !ens->eps)
+      return fail(c, TSBTS_ERR_ARG, "bad cluster count or null array");
+    if (ens->offsets[0] != 0 || ens->offsets[ens->nc] != n)
+      return fail(c, TSBTS_ERR_ARG, "offsets must run from 0 to n");
+    for (int64_t k = 0; k < ens->nc; ++k) {
+      if (ens->offsets[k + 1] <= ens->offsets[k])
+        return fail(c, TSBTS_ERR_ARG, "every cluster needs at least one body");
+      if (!(ens->eps[k] >= 0.0) || !std::isfinite(ens->eps[k]))
+        return fail(c, TSBTS_ERR_ARG, "eps must be finite and >= 0");
+    }
+    if (c->cfg.era_mode != 0)
+      return fail(c, TSBTS_ERR_ARG, "ensembles use a fixed era");
+  }
   if (!(eta > 0.0) || !std::isfinite(eta))
     return fail(c, TSBTS_ERR_ARG, "eta must be finite and > 0");
   int k_min = 0;
@@ -494,8 +610,15 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     c->fl = force_launch_shape(c->cfg.precision, c->cfg.device);
     // 32-thread blocks spread the FP64 work of small active sets over SMs
     c->correct_grid = std::max(1, std::min(c->sms * 32, (c->n + 31) / 32));
+    c->ensemble = false;
+    c->nc = 0;
     setup_bodies(c, (int)n);
-    build_plan_table(c);
+    if (ens) {
+      c->d_plans = nullptr;
+      setup_ensemble(c, *ens);
+    } else {
+      build_plan_table(c);
+    }
     Params& P = c->P;
     P = Params{};
     P.eps2 = eps * eps;
@@ -526,20 +649,26 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     launch_load_aos(c->B, dm, dr, dv, c->d_ctl, c->s);
     // Alg. 2 step 1: forces on every body, first steps
     launch_init_jdata(c->B, P, c->s);
-    ForceArgs fa = force_args_engine(c, 0);
-    fa.n_act_fixed = c->n;
-    fa.n_act_ptr = nullptr;
-    fa.nsplit_out = c->d_nsplit;
-    fa.done = nullptr;
-    ck(launch_force(c->cfg.precision, fa, c->fl, c->s), "init force");
-    launch_init_finalize(c->B, P, c->d_nsplit, c->s);
-    ck(cudaGetLastError(), "init kernels");
-    c->launches = 4;
+    if (c->ensemble) {
+      launch_ens_init(c->B, P, c->E, c->efl, c->cfg.precision, c->exact, c->s);
+      ck(cudaGetLastError(), "init kernels");
+      c->launches = 6;
+    } else {
+      ForceArgs fa = force_args_engine(c, 0);
+      fa.n_act_fixed = c->n;
+      fa.n_act_ptr = nullptr;
+      fa.nsplit_out = c->d_nsplit;
+      fa.done = nullptr;
+      ck(launch_force(c->cfg.precision, fa, c->fl, c->s), "init force");
+      launch_init_finalize(c->B, P, c->d_nsplit, c->s);
+      ck(cudaGetLastError(), "init kernels");
+      c->launches = 4;
+    }
     read_ctl(c);
     free_list(tmp);
     if (c->h_ctl->err & kErrNonFinite)
       return fail(c, TSBTS_ERR_NONFINITE, "non-finite input or initial force");
-    if (c->cfg.precision == TSBTS_MIXED && c->d_plans) {
+    if (c->cfg.precision == TSBTS_MIXED && c->d_plans && !c->ensemble) {
       // measured work plans on this device for this n (first context only;
       // later contexts reuse the cached table)
       std::vector<Plan> t;
@@ -687,9 +816,70 @@ int tsbts_step_era(tsbts_ctx* ctx, double t_end, double* t_reached) {
   }
 }
 
+int tsbts_ensemble_energy(tsbts_ctx* ctx, double* ekin, double* epot) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (!ctx->ensemble)
+    return fail(ctx, TSBTS_ERR_STATE, "context holds no ensemble");
+  try {
+    ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+    launch_ens_energy(ctx->B, ctx->P, ctx->E, ctx->t_sys, ctx->d_w, ctx->d_ek,
+                      ctx->d_ep, ctx->s);
+    ck(cudaGetLastError(), "energy kernels");
+    ctx->launches += 3;
+    if (ekin)
+      ck(cudaMemcpyAsync(ekin, ctx->d_ek, sizeof(double) * ctx->nc,
+                         cudaMemcpyDeviceToHost, ctx->s), "read energy");
+    if (epot)
+      ck(cudaMemcpyAsync(epot, ctx->d_ep, sizeof(double) * ctx->nc,
+                         cudaMemcpyDeviceToHost, ctx->s), "read energy");
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
+int tsbts_init_ensemble(tsbts_ctx* ctx, int64_t n_clusters,
+                        const int64_t* offsets, const double* m,
+                        const double* r, const double* v, const double* eps,
+                        double eta, double dt_max) {
+  if (!ctx) return TSBTS_ERR_ARG;
+  if (!offsets || n_clusters < 1)
+    return fail(ctx, TSBTS_ERR_ARG, "bad cluster count or null offsets");
+  const int64_t n = offsets[n_clusters];
+  if (m && r && v && n > 0 && n <= (1LL << 24)) {
+    for (int64_t i = 0; i < n; ++i) {
+      bool ok = std::isfinite(m[i]);
+      for (int d = 0; d < 3; ++d)
+        ok = ok && std::isfinite(r[3 * i + d]) && std::isfinite(v[3 * i + d]);
+      if (!ok)
+        return fail(ctx, TSBTS_ERR_NONFINITE,
+                    "non-finite input at body " + std::to_string(i));
+    }
+  }
+  const EnsInput in{n_clusters, offsets, eps};
+  return init_common(ctx, n, m, r, v, 0.0, eta, dt_max, true, &in);
+}
+
 int tsbts_energy(tsbts_ctx* ctx, double* ekin, double* epot, double* etot) {
   int rc = check_ready(ctx);
   if (rc) return rc;
+  if (ctx->ensemble) {
+    // totals over the clusters, each cluster's sums added in cluster order
+    std::vector<double> k(ctx->nc), p(ctx->nc);
+    rc = tsbts_ensemble_energy(ctx, k.data(), p.data());
+    if (rc) return rc;
+    double ks = 0.0, ps = 0.0;
+    for (int c = 0; c < ctx->nc; ++c) {
+      ks += k[c];
+      ps += p[c];
+    }
+    if (ekin) *ekin = ks;
+    if (epot) *epot = ps;
+    if (etot) *etot = ks + ps;
+    return TSBTS_OK;
+  }
   try {
     ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
     launch_energy(ctx->B, ctx->P, ctx->t_sys, ctx->d_w, ctx->d_eout, ctx->sms,
@@ -787,6 +977,8 @@ int tsbts_schedule_log(tsbts_ctx* ctx, int64_t capacity_entries) {
   if (rc) return rc;
   if (capacity_entries < 0)
     return fail(ctx, TSBTS_ERR_ARG, "capacity must be >= 0");
+  if (ctx->ensemble && capacity_entries > 0)
+    return fail(ctx, TSBTS_ERR_ARG, "ensembles record no schedule log");
   try {
     ck(cudaStreamSynchronize(ctx->s), "synchronize");
     free_list(ctx->lg_allocs);

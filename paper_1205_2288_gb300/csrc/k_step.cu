@@ -13,6 +13,7 @@
 // next multiple of the smallest populated step after the current block
 // time, and a per-level body count (updated by the correction kernel)
 // replaces the paper's sort by block time.
+#include "step_device.cuh"
 #include "tsbts_kernels.cuh"
 
 namespace tsbts {
@@ -70,24 +71,6 @@ __global__ void pass_setup_kernel(Bodies B, Params P, History cur) {
 // Step A: block time, active list, prediction of every body (Alg. 2
 // steps 3-4; Eq. 2; time-symmetric interpolation in passes >= 1).
 // ---------------------------------------------------------------------
-__device__ __forceinline__ void store_prediction(const Bodies& B,
-                                                 const Params& P, int j,
-                                                 const double rp[3],
-                                                 const double vp[3]) {
-  if (P.precision == 0) {
-    for (int c = 0; c < 3; ++c) {
-      B.pr[c][j] = rp[c];
-      B.pv[c][j] = vp[c];
-    }
-  } else {
-    const float xh = (float)rp[0], yh = (float)rp[1], zh = (float)rp[2];
-    B.jhi[j] = make_float4(xh, yh, zh, (float)B.m[j]);
-    B.jlo[j] = make_float4((float)(rp[0] - (double)xh),
-                           (float)(rp[1] - (double)yh),
-                           (float)(rp[2] - (double)zh), 0.f);
-    B.jv[j] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
-  }
-}
 
 __global__ void select_predict_kernel(Bodies B, Params P, History HA,
                                       History HB, int p) {
@@ -136,62 +119,7 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
     const long long nt = tj + B.dt[j];
     act = (nt == tn);
     if (nt < tn) atomicOr(&ctl->err, kErrInvariant);
-    double rp[3], vp[3];
-    bool have = false;
-    if (pass > 0 && !act) {
-      // previous-pass records A <= tn < B of body j, from the segment cache;
-      // refilled from the body's contiguous records when tn leaves it
-      const int n = B.n;
-      long long ta = B.seg_ta[j], tb = B.seg_tb[j];
-      if (!(ta <= tn && (tb < 0 || tn < tb))) {
-        int c = B.cursor[j];
-        const int end = B.hoff[j + 1];
-        if (prev.tau[c] <= tn) {
-          while (c + 1 < end && prev.tau[c + 1] <= tn) ++c;
-          B.cursor[j] = c;
-          const int nx = c + 1 < end ? c + 1 : -1;
-          ta = prev.tau[c];
-          tb = nx >= 0 ? prev.tau[nx] : -1;
-          for (int d = 0; d < 3; ++d) {
-            B.seg[(d + 0) * n + j] = prev.r[d][c];
-            B.seg[(d + 3) * n + j] = prev.v[d][c];
-            B.seg[(d + 6) * n + j] = prev.a[d][c];
-            if (nx >= 0) {
-              B.seg[(d + 9) * n + j] = prev.r[d][nx];
-              B.seg[(d + 12) * n + j] = prev.v[d][nx];
-              B.seg[(d + 15) * n + j] = prev.a[d][nx];
-            }
-          }
-        } else {
-          ta = LLONG_MAX;  // no record at or before tn: Taylor
-          tb = -1;
-        }
-        B.seg_ta[j] = ta;
-        B.seg_tb[j] = tb;
-      }
-      if (ta == tn) {
-        for (int d = 0; d < 3; ++d) {
-          rp[d] = B.seg[(d + 0) * n + j];
-          vp[d] = B.seg[(d + 3) * n + j];
-        }
-        have = true;
-      } else if (ta < tn && tb > tn) {
-        const HermiteW w = hermite_weights(ta, tb, tn, P.inv_ticks);
-        for (int d = 0; d < 3; ++d) {
-          rp[d] = hermite1(w, B.seg[(d + 0) * n + j], B.seg[(d + 3) * n + j],
-                           B.seg[(d + 9) * n + j], B.seg[(d + 12) * n + j]);
-          vp[d] = hermite1(w, B.seg[(d + 3) * n + j], B.seg[(d + 6) * n + j],
-                           B.seg[(d + 12) * n + j], B.seg[(d + 15) * n + j]);
-        }
-        have = true;
-      }
-    }
-    if (!have) {
-      const double h = __dmul_rn((double)(tn - tj), P.inv_ticks);
-      for (int d = 0; d < 3; ++d)
-        taylor1(B.r[d][j], B.v[d][j], B.a[d][j], h, rp[d], vp[d]);
-    }
-    store_prediction(B, P, j, rp, vp);
+    predict_body(B, P, prev, j, tj, tn, pass, act);
   }
   // compaction of the active list (order within a step is arbitrary)
   const unsigned bal = __ballot_sync(kFull, act);
@@ -224,81 +152,15 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
        k += gridDim.x * blockDim.x) {
     const int i = B.act[k];
     double an[3], q;
-    {
-      const double* pp = B.part;
-      an[0] = pp[0 * n_act + k];
-      an[1] = pp[1 * n_act + k];
-      an[2] = pp[2 * n_act + k];
-      q = pp[4 * n_act + k];
-      #pragma unroll 4
-      for (int sp = 1; sp < S; ++sp) {
-        pp = B.part + (long long)sp * 5 * n_act;
-        an[0] = __dadd_rn(an[0], pp[0 * n_act + k]);
-        an[1] = __dadd_rn(an[1], pp[1 * n_act + k]);
-        an[2] = __dadd_rn(an[2], pp[2 * n_act + k]);
-        q = fmax(q, pp[4 * n_act + k]);
-      }
-    }
-    if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]) ||
-        !(q >= 0.0) || isnan(q))
-      atomicOr(&ctl->err, kErrNonFinite);
-    const long long d = B.dt[i];
-    const double h = __dmul_rn((double)d, P.inv_ticks);
-    double rn[3], vn[3];
-    for (int c = 0; c < 3; ++c) {
-      double rp, vp;
-      taylor1(B.r[c][i], B.v[c][i], B.a[c][i], h, rp, vp);
-      rn[c] = rp;
-      vn[c] = __dadd_rn(B.v[c][i],
-                        __dmul_rn(__dmul_rn(0.5, __dadd_rn(B.a[c][i], an[c])),
-                                  h));
-      B.r[c][i] = rn[c];
-      B.v[c][i] = vn[c];
-      B.a[c][i] = an[c];
-    }
-    B.tau[i] = tn;
-    const double dts = __ddiv_rn(P.eta, __dsqrt_rn(q));
-    B.dts[i] = dts;
-    const long long rec = sl.nrec + k;
-    if (rec < cur.cap) {
-      cur.tau[rec] = tn;
-      for (int c = 0; c < 3; ++c) {
-        cur.r[c][rec] = rn[c];
-        cur.v[c][rec] = vn[c];
-        cur.a[c][rec] = an[c];
-      }
-      cur.dts[rec] = dts;
-      cur.body[rec] = i;
-      const int sq = B.hcnt[i];
-      cur.seq[rec] = sq;
-      B.hcnt[i] = sq + 1;
-    } else {
-      atomicOr(&ctl->err, kErrHistory);
-    }
-    int uf = 0;
-    long long c;
-    if (pass == 0) {
-      c = forward_step(tn, d, dts, P.k_min, P.k_max, &uf);
-    } else {
-      // advance the body's previous-pass cursor to the block time; the
-      // lookups below then read the few records that follow it
-      int start = B.cursor[i];
-      const int end = B.hoff[i + 1];
-      if (prev.tau[start] <= tn) {
-        while (start + 1 < end && prev.tau[start + 1] <= tn) ++start;
-        B.cursor[i] = start;
-      }
-      const double e2 = history_dts_at(prev, start, end, tn + 2 * d, dts);
-      const double e1 = history_dts_at(prev, start, end, tn + d, dts);
-      c = symmetric_step(tn, d, dts, e2, e1, P.k_min, P.k_max, P.dtmax_t,
-                         &uf);
-    }
-    if (uf) atomicAdd(&ctl->underflow, 1ULL);
-    if (c != d) {
-      atomicSub(&dh[level_of(d, P.k_max)], 1);
+    sum_partials(B.part, n_act, S, k, an, q);
+    const Corrected cr = correct_body(B, P, cur, prev, i, an, q, tn, pass,
+                                      sl.nrec + k, &ctl->err);
+    const long long c = cr.d_new;
+    if (cr.underflow) atomicAdd(&ctl->underflow, 1ULL);
+    if (c != cr.d_old) {
+      atomicSub(&dh[level_of(cr.d_old, P.k_max)], 1);
       atomicAdd(&dh[level_of(c, P.k_max)], 1);
     }
-    B.dt[i] = c;
     if (P.lg_cap > 0) {
       const long long e = sl.lg_base + k;
       if (e < P.lg_cap) {
@@ -678,6 +540,11 @@ void launch_energy(const Bodies& B, const Params& P, long long T, double* w,
   energy_pair_kernel<NT, TJ><<<g, NT, 0, s>>>(B, P.eps2, w);
   energy_sum_kernel<<<1, 32, 0, s>>>(B, w, out);
   (void)sms;
+}
+
+void launch_energy_predict(const Bodies& B, const Params& P, long long T,
+                           cudaStream_t s) {
+  energy_predict_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, P, T);
 }
 
 }  // namespace tsbts

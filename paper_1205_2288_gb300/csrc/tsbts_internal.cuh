@@ -125,6 +125,31 @@ struct Params {
   long long lg_cap;
 };
 
+// An ensemble of independent clusters integrated together: bodies of
+// cluster c are off[c] .. off[c+1]-1 in the Bodies arrays; each cluster
+// keeps its own block time and level counts, and every global block step
+// advances every cluster that has not finished the pass by one of its own
+// block steps.
+struct Ens {
+  int nc;
+  const int* off;        // nc + 1 body offsets
+  const int* cl;         // cluster of each body
+  const double* eps2;    // per cluster
+  const float* eps2f;
+  long long* tau_c;      // per cluster: block time before this step
+  long long* tau_next;   // per cluster: this step's block time, or
+                         // LLONG_MAX when the cluster has finished the pass
+  int* cnt;              // per cluster: active bodies this step
+  int* hist;             // nc * kMaxLevels level counts
+  int* act;              // n: active list of cluster c at off[c] (local ids)
+  struct Plan* plan;     // per cluster: force plan this step
+  int* item_off;         // nc + 1: prefix of force work items
+  int* act_base;         // nc + 1: prefix of active counts
+  long long* part_off;   // nc + 1: prefix of partial sums (doubles)
+  int* totals;           // [0] items, [1] active bodies, [2] clusters
+                         // still stepping, [3] record base of this step
+};
+
 // Work plan of one force launch: IG active bodies per work item (128 / IG
 // threads per body), n_g i-groups, S j-splits of `chunk` j each; direct = 1
 // reads j records straight from global memory instead of staging tiles in

@@ -28,5 +28,28 @@ void launch_init_finalize(const Bodies& B, const Params& P, const int* nsplit,
                           cudaStream_t s);
 void launch_energy(const Bodies& B, const Params& P, long long T, double* w,
                    double* out, int sms, cudaStream_t s);
+// Eq. 2 prediction of every body to tick T into the FP64 j arrays
+void launch_energy_predict(const Bodies& B, const Params& P, long long T,
+                           cudaStream_t s);
+
+// ensembles of independent clusters (k_ensemble.cu)
+int ens_max_clusters();
+ForceLaunch ens_force_launch_shape(int precision, int device);
+void launch_ens_pass_begin(const Ens& E, long long tau_s, cudaStream_t s);
+void launch_ens_pass_setup(const Bodies& B, const Params& P, const Ens& E,
+                           const History& cur, cudaStream_t s);
+// one global block step (five launches); ev0/ev1 (nullable) bracket the
+// force launch
+void launch_ens_step(const Bodies& B, const Params& P, const Ens& E,
+                     const History& HA, const History& HB,
+                     const ForceLaunch& fl, int precision, int exact,
+                     cudaEvent_t ev0, cudaEvent_t ev1, unsigned evflags,
+                     cudaStream_t s);
+void launch_ens_init(const Bodies& B, const Params& P, const Ens& E,
+                     const ForceLaunch& fl, int precision, int exact,
+                     cudaStream_t s);
+void launch_ens_energy(const Bodies& B, const Params& P, const Ens& E,
+                       long long T, double* w, double* ek, double* ep,
+                       cudaStream_t s);
 
 }  // namespace tsbts

@@ -41,6 +41,7 @@ EXPORTS = (
     "tsbts_set_timing", "tsbts_schedule_log", "tsbts_schedule_size",
     "tsbts_schedule_get", "tsbts_last_error", "tsbts_destroy", "tsbts_force",
     "tsbts_release_scratch", "tsbts_version", "tsbts_force_static",
+    "tsbts_init_ensemble", "tsbts_ensemble_energy",
 )
 
 
@@ -91,6 +92,9 @@ def lib():
                                  C.c_double]
         L.tsbts_init_device.argtypes = [VP, I64, VP, VP, VP, C.c_double,
                                         C.c_double, C.c_double]
+        L.tsbts_init_ensemble.argtypes = [VP, I64, I64P, DP, DP, DP, DP,
+                                          C.c_double, C.c_double]
+        L.tsbts_ensemble_energy.argtypes = [VP, DP, DP]
         L.tsbts_step_era.argtypes = [VP, C.c_double, DP]
         L.tsbts_energy.argtypes = [VP, DP, DP, DP]
         L.tsbts_state.argtypes = [VP, DP, DP, DP, DP, DP, I64P, I64P]
@@ -159,6 +163,27 @@ def tsbts_init_device(ctx, m, r, v, eps, eta, dt_max):
     _check(lib().tsbts_init_device(ctx, n, m.data_ptr(), r.data_ptr(),
                                    v.data_ptr(), float(eps), float(eta),
                                    float(dt_max)), ctx)
+
+
+def tsbts_init_ensemble(ctx, offsets, m, r, v, eps, eta, dt_max):
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    m = np.ascontiguousarray(m, np.float64)
+    r = np.ascontiguousarray(r, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    eps = np.ascontiguousarray(eps, np.float64)
+    nc = offsets.shape[0] - 1
+    if eps.shape != (nc,) or r.shape != (m.shape[0], 3) or \
+            v.shape != (m.shape[0], 3):
+        raise ValueError("shapes: offsets (nc+1,), eps (nc,), r and v (n, 3)")
+    _check(lib().tsbts_init_ensemble(ctx, nc, _p(offsets, I64P), _p(m), _p(r),
+                                     _p(v), _p(eps), float(eta),
+                                     float(dt_max)), ctx)
+
+
+def tsbts_ensemble_energy(ctx, n_clusters):
+    ek, ep = np.zeros(n_clusters), np.zeros(n_clusters)
+    _check(lib().tsbts_ensemble_energy(ctx, _p(ek), _p(ep)), ctx)
+    return ek, ep
 
 
 def tsbts_step_era(ctx, t_end) -> float:
@@ -333,3 +358,38 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Ensemble(Simulation):
+    """Independent clusters integrated together (tsbts_init_ensemble).
+
+    offsets[c] .. offsets[c+1]-1 are cluster c's bodies; eps[c] its
+    softening. Fixed era only."""
+
+    def __init__(self, offsets, m, r, v, *, eps, eta, dt_max,
+                 precision=TSBTS_FP64, n_iter=3, era_log2=3, k_max=20,
+                 exact_order=-1, device=0, stream=None, graph_steps=32):
+        cfg = tsbts_config_default()
+        cfg.precision = precision
+        cfg.n_iter = n_iter
+        cfg.era_mode = 0
+        cfg.era_log2 = era_log2
+        cfg.k_max = k_max
+        cfg.exact_order = exact_order
+        cfg.device = device
+        cfg.stream = stream
+        cfg.graph_steps = graph_steps
+        self.cfg = cfg
+        self.k_max = k_max
+        self.n = int(np.asarray(m).shape[0])
+        self.n_clusters = int(np.asarray(offsets).shape[0] - 1)
+        self.ctx = tsbts_create(cfg)
+        try:
+            tsbts_init_ensemble(self.ctx, offsets, m, r, v, eps, eta, dt_max)
+        except Exception:
+            tsbts_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def cluster_energy(self):
+        return tsbts_ensemble_energy(self.ctx, self.n_clusters)

@@ -1,0 +1,127 @@
+"""Ensembles of independent clusters (tsbts_init_ensemble): every cluster,
+integrated together with the others on the GPU, must match the FP64 oracle
+run on that cluster alone. With FP64 ascending-j sums each cluster's block
+schedule, state and energy are bit-identical; mixed precision is held to
+the energy bar of the single-system tests."""
+import numpy as np
+import pytest
+
+from paper_1205_2288_gb300 import inputs, tsbts
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def need_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+
+
+def make_clusters(sizes, seed):
+    ms, rs, vs = [], [], []
+    for c, n in enumerate(sizes):
+        m = inputs.salpeter_masses(n, seed=1000 * seed + 2 * c)
+        m, r, v = inputs.plummer(n, seed=1000 * seed + 2 * c + 1, masses=m)
+        ms.append(m)
+        rs.append(r)
+        vs.append(v)
+    off = np.zeros(len(sizes) + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    eps = 4.0 / np.asarray(sizes, np.float64)
+    return off, np.concatenate(ms), np.concatenate(rs), np.concatenate(vs), eps
+
+
+KW = dict(eta=0.02, dt_max=1 / 8, n_iter=3, era_log2=3, k_max=20)
+
+
+def oracle_clusters(orc, off, m, r, v, eps, t_end, **kw):
+    out = []
+    for c in range(len(off) - 1):
+        a, b = off[c], off[c + 1]
+        s = orc.Sim(m[a:b], r[a:b], v[a:b], eps=eps[c], era_mode=0, **kw)
+        e0 = s.energy()
+        s.run(t_end)
+        out.append((s.state(), e0, s.energy(), s.stats()))
+    return out
+
+
+def test_ensemble_fp64_bit_exact_per_cluster(orc):
+    sizes = [64, 100, 37, 300, 77, 512, 1]
+    off, m, r, v, eps = make_clusters(sizes, seed=1)
+    ref = oracle_clusters(orc, off, m, r, v, eps, 0.25, **KW)
+    g = tsbts.Ensemble(off, m, r, v, eps=eps, **KW)
+    ek0, ep0 = g.cluster_energy()
+    g.step_era(0.25)
+    st = g.state()
+    ek, ep = g.cluster_energy()
+    for c in range(len(sizes)):
+        a, b = off[c], off[c + 1]
+        so, e0, e1, _ = ref[c]
+        for key in ("r", "v", "a", "tau", "dt"):
+            np.testing.assert_array_equal(st[key][a:b], so[key],
+                                          err_msg=f"cluster {c} {key}")
+        assert (ek0[c], ep0[c]) == e0
+        assert (ek[c], ep[c]) == e1
+    # interactions: every cluster's own n_act * N_c, summed
+    assert g.stats()["interactions"] == sum(x[3]["interactions"] for x in ref)
+    assert g.stats()["kernel_launches"] > 0
+
+
+def test_single_cluster_ensemble_equals_single_system():
+    off, m, r, v, eps = make_clusters([200], seed=2)
+    e = tsbts.Ensemble(off, m, r, v, eps=eps, **KW)
+    s = tsbts.Simulation(m, r, v, eps=float(eps[0]), **KW)
+    e.step_era(0.25)
+    s.step_era(0.25)
+    a, b = e.state(), s.state()
+    for key in ("r", "v", "a", "tau", "dt"):
+        np.testing.assert_array_equal(a[key], b[key])
+    assert e.stats()["block_steps"] == s.stats()["block_steps"]
+
+
+@pytest.mark.parametrize("graph_steps", [0, 32])
+def test_ensemble_mixed_energy_and_trajectories(orc, graph_steps):
+    sizes = [64, 500, 1500, 200, 3000, 90]
+    off, m, r, v, eps = make_clusters(sizes, seed=3)
+    kw = dict(KW, eta=0.01)
+    ref = oracle_clusters(orc, off, m, r, v, eps, 0.125, **kw)
+    g = tsbts.Ensemble(off, m, r, v, eps=eps, precision=tsbts.TSBTS_MIXED,
+                       graph_steps=graph_steps, **kw)
+    ek0, ep0 = g.cluster_energy()
+    g.step_era(0.125)
+    ek, ep = g.cluster_energy()
+    st = g.state()
+    for c in range(len(sizes)):
+        a, b = off[c], off[c + 1]
+        so, e0, e1, _ = ref[c]
+        E0 = sum(e0)
+        de_o = abs(sum(e1) / E0 - 1)
+        de_g = abs((ek[c] + ep[c]) / (ek0[c] + ep0[c]) - 1)
+        assert de_g <= 2 * de_o + 1e-7, (c, de_g, de_o)
+        assert np.abs(st["r"][a:b] - so["r"]).max() < 1e-4
+
+
+def test_ensemble_argument_errors():
+    off, m, r, v, eps = make_clusters([10, 20], seed=4)
+    cfg = tsbts.tsbts_config_default()
+    ctx = tsbts.tsbts_create(cfg)
+    try:
+        bad = off.copy()
+        bad[1] = 0     # an empty cluster
+        with pytest.raises(tsbts.TsbtsError) as e:
+            tsbts.tsbts_init_ensemble(ctx, bad, m, r, v, eps, 0.02, 1 / 8)
+        assert e.value.code == tsbts.TSBTS_ERR_ARG
+        with pytest.raises(tsbts.TsbtsError) as e:
+            tsbts.tsbts_init_ensemble(ctx, off, m, r, v, -eps, 0.02, 1 / 8)
+        assert e.value.code == tsbts.TSBTS_ERR_ARG
+    finally:
+        tsbts.tsbts_destroy(ctx)
+    cfg.era_mode = 1
+    ctx = tsbts.tsbts_create(cfg)
+    try:
+        with pytest.raises(tsbts.TsbtsError) as e:
+            tsbts.tsbts_init_ensemble(ctx, off, m, r, v, eps, 0.02, 1 / 8)
+        assert e.value.code == tsbts.TSBTS_ERR_ARG
+    finally:
+        tsbts.tsbts_destroy(ctx)

@@ -141,6 +141,10 @@ def test_history_growth_reruns_the_era(orc):
     o, g, _, _ = run_pair(orc, m, r, v, 1.0, log=False, **kw)
     assert g.stats()["era_restarts"] >= 1
     assert_same_state(o, g)
+    # only the kept run of a re-run era is counted
+    assert g.stats()["block_steps"] == o.stats()["block_steps"]
+    assert g.stats()["interactions"] == o.stats()["interactions"]
+    assert g.stats()["passes"] == o.stats()["passes"]
 
 
 def test_fp64_jsplit_path_tracks_oracle(orc):
