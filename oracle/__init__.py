@@ -2,7 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the bench's
 CPU-baseline leg may import this package. It is built from the plain C in
-``tsbts_oracle.c`` with gcc and shares nothing with the CUDA library.
+``tsbts_oracle.c`` (integrator) and ``tsbts_adjoint.c`` (frozen-schedule
+replay and its reverse mode) with gcc and shares nothing with the CUDA
+library.
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tsbts_oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "tsbts_adjoint.c")
 _HDR = os.path.join(_HERE, "tsbts_oracle.h")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_LIBDIR, "liboracle.so")
@@ -38,12 +41,13 @@ class OrcCfg(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, OpenMP over bodies)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(x) for x in (_SRC, _SRC_ADJ, _HDR))
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, _SRC_ADJ,
+           "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -85,6 +89,13 @@ def lib():
             L.orc_destroy.argtypes = [C.c_void_p]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
+            sched = [I64, I64P, I64P, I32P]
+            L.orc_replay.argtypes = [I64, DP, DP, DP, C.c_double, C.c_int,
+                                     *sched, DP, DP]
+            L.orc_replay_vjp.argtypes = [I64, DP, DP, DP, C.c_double, C.c_int,
+                                         *sched, DP, DP, DP, DP, DP]
+            L.orc_loss_msr.argtypes = [I64, DP, DP, DP, DP]
+            L.orc_loss_msr.restype = C.c_double
             _lib = L
     return _lib
 
@@ -154,6 +165,73 @@ def hermite(ta, tb, t, k_max, ra, va, aa, rb, vb, ab):
     lib().orc_hermite(int(ta), int(tb), int(t), int(k_max),
                       *[_p(x) for x in args], _p(ro), _p(vo))
     return ro, vo
+
+
+def final_pass(sched, era=-1):
+    """The block schedule of one era's last pass, from a schedule log:
+    (step_tau, step_off, act) with the active bodies ascending per step."""
+    eras = np.unique(sched["era"])
+    e = eras[era]
+    sel = sched["era"] == e
+    last = sched["pass_"][sel].max()
+    sel &= sched["pass_"] == last
+    off = np.concatenate([[0], np.cumsum(sched["n_act"])]).astype(np.int64)
+    steps = np.nonzero(sel)[0]
+    tau = sched["tau"][steps].astype(np.int64)
+    parts = [np.sort(sched["idx"][off[k]:off[k + 1]]) for k in steps]
+    step_off = np.concatenate([[0], np.cumsum([len(x) for x in parts])])
+    act = np.concatenate(parts) if parts else np.zeros(0, np.int32)
+    return (np.ascontiguousarray(tau), step_off.astype(np.int64),
+            np.ascontiguousarray(act, dtype=np.int32))
+
+
+def _sched_args(schedule):
+    tau, off, act = schedule
+    tau = np.ascontiguousarray(tau, dtype=np.int64)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    act = np.ascontiguousarray(act, dtype=np.int32)
+    return (tau, off, act), [tau.shape[0], _p(tau, I64P), _p(off, I64P),
+                             _p(act, I32P)]
+
+
+def replay(m, r0, v0, eps, k_max, schedule):
+    """Final (r, v) of the Taylor replay of a frozen schedule (R14)."""
+    m, r0, v0 = _d(m), _d(r0), _d(v0)
+    keep, sa = _sched_args(schedule)
+    r, v = np.zeros_like(r0), np.zeros_like(v0)
+    lib().orc_replay(m.shape[0], _p(m), _p(r0), _p(v0), float(eps),
+                     int(k_max), *sa, _p(r), _p(v))
+    return r, v
+
+
+def replay_vjp(m, r0, v0, eps, k_max, schedule, gr_T, gv_T):
+    """Cotangents (g_r0, g_v0, g_m) of the replay for final cotangents."""
+    m, r0, v0 = _d(m), _d(r0), _d(v0)
+    gr_T, gv_T = _d(gr_T), _d(gv_T)
+    keep, sa = _sched_args(schedule)
+    g_r0, g_v0, g_m = np.zeros_like(r0), np.zeros_like(v0), np.zeros_like(m)
+    lib().orc_replay_vjp(m.shape[0], _p(m), _p(r0), _p(v0), float(eps),
+                         int(k_max), *sa, _p(gr_T), _p(gv_T), _p(g_r0),
+                         _p(g_v0), _p(g_m))
+    return g_r0, g_v0, g_m
+
+
+def loss_msr(m, r):
+    """L = sum m |r|^2 / sum m with its partials (L, dL/dr, dL/dm)."""
+    m, r = _d(m), _d(r)
+    g_r, g_m = np.zeros_like(r), np.zeros_like(m)
+    L = lib().orc_loss_msr(m.shape[0], _p(m), _p(r), _p(g_r), _p(g_m))
+    return L, g_r, g_m
+
+
+def loss_grad(m, r0, v0, eps, k_max, schedule):
+    """The loss of the replayed final positions and its gradient with
+    respect to r0, v0 and m (chain rule through orc_replay_vjp)."""
+    rT, _ = replay(m, r0, v0, eps, k_max, schedule)
+    L, g_rT, g_mL = loss_msr(m, rT)
+    g_r0, g_v0, g_m = replay_vjp(m, r0, v0, eps, k_max, schedule, g_rT,
+                                 np.zeros_like(g_rT))
+    return L, g_r0, g_v0, g_m + g_mL
 
 
 class Sim:

@@ -93,6 +93,38 @@ void orc_destroy(orc_sim* s);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 
+/* Adjoint of a frozen block schedule (reading R14): the schedule of an
+ * era's final pass is replayed with Taylor prediction only, as in a first
+ * pass, and differentiated in reverse mode. The schedule is n_steps block
+ * steps; step s ends at tick step_tau[s] (strictly increasing) and moves
+ * the bodies act[step_off[s] .. step_off[s+1]). Start: (r0, v0) at tick 0
+ * with a0 = force on every body at r0. Each step predicts every body with
+ * Eq. 2 from its own time, computes the force (Eq. 3 sums) on the active
+ * bodies at the predicted positions and corrects them with Eq. 1 over
+ * their own step (block time minus their previous time). */
+
+/* Forward replay: final positions and velocities (each body at the time of
+ * its last step, or at tick 0 if it never moves). */
+void orc_replay(int64_t n, const double* m, const double* r0, const double* v0,
+                double eps, int k_max, int64_t n_steps, const int64_t* step_tau,
+                const int64_t* step_off, const int32_t* act, double* r_out,
+                double* v_out);
+
+/* Reverse mode: given cotangents gr_T, gv_T of the final positions and
+ * velocities, the cotangents of r0, v0 and m. Gradients with respect to
+ * m are summed over every force evaluation, the initial one included. */
+void orc_replay_vjp(int64_t n, const double* m, const double* r0,
+                    const double* v0, double eps, int k_max, int64_t n_steps,
+                    const int64_t* step_tau, const int64_t* step_off,
+                    const int32_t* act, const double* gr_T, const double* gv_T,
+                    double* g_r0, double* g_v0, double* g_m);
+
+/* Mass-weighted mean-square radius about the origin,
+ * L = sum_i m_i |r_i|^2 / sum_i m_i, with its partial derivatives with
+ * respect to r (g_r) and m (g_m); either may be NULL. */
+double orc_loss_msr(int64_t n, const double* m, const double* r, double* g_r,
+                    double* g_m);
+
 #ifdef __cplusplus
 }
 #endif
