@@ -225,6 +225,92 @@ int tsbts_force_static(int precision, int exact_order, int64_t n,
                        double eps, int64_t n_act, const int32_t* idx,
                        double* a, double* phi, double* q, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Adjoint of a frozen block schedule.
+ *
+ * The paper defines no adjoint; this is the reading taken here. The
+ * gradient of a function of the bodies' final state with respect to their
+ * initial positions, velocities and masses is taken through one era's
+ * final-pass block schedule, replayed as plain block steps: every body is
+ * predicted to the block time with Eq. 2 from its own time, the active
+ * bodies get the force sums of Eq. 3 at the predicted positions and are
+ * corrected with Eq. 1 over their own step. The schedule (block times and
+ * active sets) is held fixed and is not differentiated; the step criterion
+ * plays no part. Reverse mode runs the chain rule step by step backwards,
+ * with the force's vector-Jacobian product computed by dedicated kernels.
+ *
+ * A context that holds an adjoint may also hold an integrator (tsbts_init)
+ * or an ensemble; they share only the device, the stream and the precision.
+ * --------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t steps;               /* block steps of the schedule */
+  int64_t entries;             /* sum of the active counts */
+  int64_t checkpoint_every;    /* 0: the whole schedule is taped */
+  int64_t checkpoints;         /* full-state checkpoints held */
+  int64_t tape_entries;        /* pre-step records the tape holds */
+  int64_t tape_bytes;          /* device bytes of the tape */
+  int64_t checkpoint_bytes;    /* device bytes of the checkpoints */
+  int64_t device_bytes;        /* all device memory of the adjoint */
+  int64_t pairs_forward;       /* pair terms of the last forward call */
+  int64_t pairs_backward;      /* pair terms of the last reverse sweep
+                                  (force VJP both ends, plus recomputed
+                                  forward steps) */
+  double forward_ms;           /* device time of the last forward call */
+  double backward_ms;          /* device time of the last reverse sweep */
+  int64_t kernel_launches;     /* kernels launched by the adjoint */
+} tsbts_adjoint_stats;
+
+/* Set up the adjoint of a schedule over n bodies with softening eps >= 0.
+ * The schedule is n_steps block steps in HOST arrays: step s ends at tick
+ * step_tau[s] (2^k_max ticks per time unit, strictly increasing, > 0) and
+ * moves the bodies act[step_off[s] .. step_off[s+1]) (step_off[0] = 0,
+ * every step non-empty, each body at most once per step, each in [0, n)).
+ * Arrays are copied. checkpoint_every = 0 tapes the pre-step state of
+ * every entry during the forward replay (80 bytes per entry); K > 0 keeps
+ * only a full-state checkpoint every K steps (80 bytes per body each) and
+ * recomputes each K-step segment, taped, during the reverse sweep.
+ * Precision, k_max, exact_order, device and stream come from the context's
+ * config. TSBTS_ERR_ARG: a bad size or schedule. */
+int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps,
+                       int64_t n_steps, const int64_t* step_tau,
+                       const int64_t* step_off, const int32_t* act,
+                       int64_t checkpoint_every);
+
+/* Forward replay from masses m[n], positions r0[n*3] and velocities
+ * v0[n*3] at tick 0 (initial accelerations: the force on every body at
+ * r0). r_T, v_T [n*3] (each may be NULL) receive each body's final state,
+ * at the time of its last step (tick 0 if it never moves). device_ptrs = 1:
+ * every pointer is a DEVICE pointer on the context's device, read and
+ * written in order on the context's stream; 0: HOST pointers. The call
+ * returns when the results are written. The inputs are kept for
+ * tsbts_adjoint_vjp. TSBTS_ERR_NONFINITE: non-finite input or force. */
+int tsbts_adjoint_forward(tsbts_ctx* ctx, const double* m, const double* r0,
+                          const double* v0, double* r_T, double* v_T,
+                          int device_ptrs);
+
+/* Reverse mode of the last forward replay: given the cotangents gr_T, gv_T
+ * [n*3] of the final positions and velocities (either may be NULL for
+ * zero), writes g_r0, g_v0 [n*3] and g_m [n] (each may be NULL), the
+ * cotangents of r0, v0 and m; the mass cotangent sums every force
+ * evaluation, the initial one included. Pointers as in
+ * tsbts_adjoint_forward. TSBTS_ERR_STATE: no forward replay yet. */
+int tsbts_adjoint_vjp(tsbts_ctx* ctx, const double* gr_T, const double* gv_T,
+                      double* g_r0, double* g_v0, double* g_m,
+                      int device_ptrs);
+
+/* Forward replay and reverse mode of the loss
+ *   L = sum_i m_i |r_i(T)|^2 / sum_i m_i
+ * (the mass-weighted mean-square radius about the origin of the final
+ * positions): *loss and the gradients g_r0, g_v0 [n*3], g_m [n] (each may
+ * be NULL; dL/dm includes the loss's own dependence on m). Pointers as in
+ * tsbts_adjoint_forward (with device_ptrs = 1, loss is a device double). */
+int tsbts_adjoint_loss_grad(tsbts_ctx* ctx, const double* m, const double* r0,
+                            const double* v0, double* loss, double* g_r0,
+                            double* g_v0, double* g_m, int device_ptrs);
+
+int tsbts_adjoint_get_stats(tsbts_ctx* ctx, tsbts_adjoint_stats* out);
+
 /* Library version string. */
 const char* tsbts_version(void);
 

@@ -52,4 +52,101 @@ void launch_ens_energy(const Bodies& B, const Params& P, const Ens& E,
                        long long T, double* w, double* ek, double* ep,
                        cudaStream_t s);
 
+// ---------------------------------------------------------------------
+// Adjoint of a frozen block schedule (k_adjoint.cu).
+// ---------------------------------------------------------------------
+
+// replay state of every body, structure of arrays
+struct AdjState {
+  double* r[3];
+  double* v[3];
+  double* a[3];
+  long long* tau;
+};
+// cotangents of the replay state and of the masses
+struct AdjCot {
+  double* gr[3];
+  double* gv[3];
+  double* ga[3];
+  double* gm;
+};
+// pre-step state of schedule entries base, base + 1, ...: components
+// r (0..2), v (3..5), a (6..8); tau == nullptr: no tape
+struct AdjTape {
+  double* x[9];
+  long long* tau;
+  long long base;
+};
+// Eq. 2 prediction of every body to the block time: FP64 positions, and
+// for the mixed path the packed j records (p_hi, m) and (p_lo, 0)
+struct AdjPred {
+  const double* m;
+  double* p[3];
+  float4* jhi;
+  float4* jlo;
+};
+// the active bodies of the step being reversed, by slot k (their order in
+// the schedule): the force cotangent lam, the cotangent gp0 of the new
+// position, the predicted position (FP64 ap; mixed ahi/alo) and lam in
+// FP32 (alam); slot[j] is body j's slot, -1 if it is not active
+struct AdjSlots {
+  double* lam[3];
+  double* gp0[3];
+  double* ap[3];
+  float4* ahi;
+  float4* alo;
+  float4* alam;
+  int* slot;
+};
+// work split of one side of the force vector-Jacobian product: `tpt`
+// threads per target (a power of two <= 32), S splits of `chunk` sources,
+// `groups` blocks of 128 / tpt targets per split
+struct VjpSide {
+  int tpt, S, chunk, groups;
+};
+// i side: targets are the active bodies, sources every body; j side:
+// targets every body, sources the active bodies
+struct VjpShape {
+  VjpSide si, sj;
+};
+VjpShape vjp_shape(int n, int n_act, int sms);
+
+void launch_adj_load(int n, const double* m_in, const double* r_in,
+                     const double* v_in, int mixed, double* m_out,
+                     const AdjState& St, const AdjPred& P, int* err,
+                     cudaStream_t s);
+void launch_adj_init_accel(int n, const double* part, const int* nsplit,
+                           const AdjState& St, int* err, cudaStream_t s);
+void launch_adj_predict(int n, long long T, double inv_ticks, int mixed,
+                        const AdjState& St, const AdjPred& P, cudaStream_t s);
+void launch_adj_correct(int n_act, const int* idx, long long T,
+                        double inv_ticks, const double* part,
+                        const int* nsplit, const AdjState& St,
+                        const AdjPred& P, const AdjTape& Tp, long long e0,
+                        int* err, cudaStream_t s);
+void launch_adj_back_prep(int n, long long T, double inv_ticks, long long e_lo,
+                          int all, int mixed, const AdjState& St,
+                          const AdjTape& Tp, long long* cur_e,
+                          const long long* prev_e, const AdjCot& C,
+                          const AdjPred& P, const AdjSlots& Sl,
+                          cudaStream_t s);
+void launch_adj_vjp(int mixed, int n, int n_act, const int* idx, double eps2,
+                    const AdjPred& P, const AdjSlots& Sl, const VjpShape& V,
+                    double* part_i, double* part_j, cudaStream_t s);
+void launch_adj_back_finalize(int n, int n_act, long long T, double inv_ticks,
+                              const VjpShape& V, const double* part_i,
+                              const double* part_j, const AdjPred& P,
+                              const AdjSlots& Sl, const AdjState& St,
+                              const AdjCot& C, int* err, cudaStream_t s);
+// L = sum m |r|^2 / sum m into out[0] (out[1] = sum m) and the cotangent
+// seeds dL/dr, dL/dm (velocity and acceleration cotangents zero)
+void launch_adj_loss(int n, const double* m, const AdjState& St, double* out,
+                     const AdjCot& C, cudaStream_t s);
+// seeds from (n, 3) cotangents of the final r and v (nullable: zero)
+void launch_adj_seed(int n, const double* gr, const double* gv,
+                     const AdjCot& C, cudaStream_t s);
+// three structure-of-arrays components -> row-major (n, 3)
+void launch_soa_to_aos(int n, double* const src[3], double* dst,
+                       cudaStream_t s);
+
 }  // namespace tsbts

@@ -41,7 +41,9 @@ EXPORTS = (
     "tsbts_set_timing", "tsbts_schedule_log", "tsbts_schedule_size",
     "tsbts_schedule_get", "tsbts_last_error", "tsbts_destroy", "tsbts_force",
     "tsbts_release_scratch", "tsbts_version", "tsbts_force_static",
-    "tsbts_init_ensemble", "tsbts_ensemble_energy",
+    "tsbts_init_ensemble", "tsbts_ensemble_energy", "tsbts_adjoint_init",
+    "tsbts_adjoint_forward", "tsbts_adjoint_vjp", "tsbts_adjoint_loss_grad",
+    "tsbts_adjoint_get_stats",
 )
 
 
@@ -59,6 +61,18 @@ class tsbts_stats(C.Structure):
                 ("era_restarts", I64), ("history_capacity", I64),
                 ("t_sys_ticks", I64), ("force_ms", C.c_double),
                 ("force_launches", I64), ("kernel_launches", I64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class tsbts_adjoint_stats(C.Structure):
+    _fields_ = [("steps", I64), ("entries", I64), ("checkpoint_every", I64),
+                ("checkpoints", I64), ("tape_entries", I64),
+                ("tape_bytes", I64), ("checkpoint_bytes", I64),
+                ("device_bytes", I64), ("pairs_forward", I64),
+                ("pairs_backward", I64), ("forward_ms", C.c_double),
+                ("backward_ms", C.c_double), ("kernel_launches", I64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -113,6 +127,14 @@ def lib():
         L.tsbts_force_static.argtypes = [C.c_int, C.c_int, I64, VP, VP, VP,
                                          C.c_double, I64, VP, VP, VP, VP, VP]
         L.tsbts_release_scratch.argtypes = []
+        L.tsbts_adjoint_init.argtypes = [VP, I64, C.c_double, I64, I64P,
+                                         I64P, I32P, I64]
+        L.tsbts_adjoint_forward.argtypes = [VP, VP, VP, VP, VP, VP, C.c_int]
+        L.tsbts_adjoint_vjp.argtypes = [VP, VP, VP, VP, VP, VP, C.c_int]
+        L.tsbts_adjoint_loss_grad.argtypes = [VP, VP, VP, VP, VP, VP, VP, VP,
+                                              C.c_int]
+        L.tsbts_adjoint_get_stats.argtypes = [VP,
+                                              C.POINTER(tsbts_adjoint_stats)]
         L.tsbts_version.argtypes = []
         L.tsbts_version.restype = C.c_char_p
         _lib = L
@@ -284,6 +306,110 @@ def tsbts_version() -> str:
     return lib().tsbts_version().decode()
 
 
+# --- adjoint of a frozen block schedule -----------------------------------
+
+def final_pass_schedule(sched, era=-1):
+    """(step_tau, step_off, act) of one era's last pass from a schedule log
+    (tsbts_schedule_get), active bodies ascending within each step."""
+    eras = np.unique(sched["era"])
+    e = eras[era]
+    keep = sched["era"] == e
+    keep &= sched["pass_"] == sched["pass_"][keep].max()
+    off = np.zeros(len(sched["n_act"]) + 1, np.int64)
+    np.cumsum(sched["n_act"], out=off[1:])
+    steps = np.flatnonzero(keep)
+    parts = [np.sort(sched["idx"][off[k]:off[k + 1]]) for k in steps]
+    step_off = np.zeros(len(parts) + 1, np.int64)
+    np.cumsum([len(x) for x in parts], out=step_off[1:])
+    act = (np.concatenate(parts) if parts else np.zeros(0)).astype(np.int32)
+    return (np.ascontiguousarray(sched["tau"][steps], dtype=np.int64),
+            step_off, act)
+
+
+def tsbts_adjoint_init(ctx, n, eps, schedule, checkpoint_every=0):
+    tau, off, act = (np.ascontiguousarray(schedule[0], np.int64),
+                     np.ascontiguousarray(schedule[1], np.int64),
+                     np.ascontiguousarray(schedule[2], np.int32))
+    if off.shape[0] != tau.shape[0] + 1:
+        raise ValueError("step_off must have one more entry than step_tau")
+    _check(lib().tsbts_adjoint_init(ctx, int(n), float(eps), tau.shape[0],
+                                    _p(tau, I64P), _p(off, I64P),
+                                    _p(act, I32P), int(checkpoint_every)), ctx)
+
+
+def _ptrs(arrays, n, device):
+    """Raw pointers of host numpy arrays or CUDA tensors (None -> NULL)."""
+    out = []
+    for a in arrays:
+        if a is None:
+            out.append(None)
+        elif device:
+            if not (a.is_cuda and a.is_contiguous()):
+                raise ValueError("device arrays must be contiguous CUDA "
+                                 "tensors")
+            out.append(a.data_ptr())
+        else:
+            if a.dtype != np.float64 or not a.flags.c_contiguous:
+                raise ValueError("host arrays must be contiguous float64")
+            out.append(a.ctypes.data)
+    return out
+
+
+def tsbts_adjoint_forward(ctx, m, r0, v0, r_T=None, v_T=None, device=False):
+    """Forward replay; host numpy (default) or CUDA tensors (device=True).
+    Host inputs are converted; host outputs are allocated if None."""
+    if not device:
+        m, r0, v0 = (np.ascontiguousarray(x, np.float64) for x in (m, r0, v0))
+        n = m.shape[0]
+        r_T = np.zeros((n, 3)) if r_T is None else r_T
+        v_T = np.zeros((n, 3)) if v_T is None else v_T
+    n = m.shape[0]
+    _check(lib().tsbts_adjoint_forward(
+        ctx, *_ptrs((m, r0, v0, r_T, v_T), n, device), int(device)), ctx)
+    return r_T, v_T
+
+
+def tsbts_adjoint_vjp(ctx, gr_T, gv_T, g_r0=None, g_v0=None, g_m=None,
+                      device=False, n=None):
+    if not device:
+        gr_T = None if gr_T is None else np.ascontiguousarray(gr_T,
+                                                              np.float64)
+        gv_T = None if gv_T is None else np.ascontiguousarray(gv_T,
+                                                              np.float64)
+        n = n if n is not None else (gr_T if gr_T is not None
+                                     else gv_T).shape[0]
+        g_r0 = np.zeros((n, 3)) if g_r0 is None else g_r0
+        g_v0 = np.zeros((n, 3)) if g_v0 is None else g_v0
+        g_m = np.zeros(n) if g_m is None else g_m
+    _check(lib().tsbts_adjoint_vjp(
+        ctx, *_ptrs((gr_T, gv_T, g_r0, g_v0, g_m), n, device), int(device)),
+        ctx)
+    return g_r0, g_v0, g_m
+
+
+def tsbts_adjoint_loss_grad(ctx, m, r0, v0, loss=None, g_r0=None, g_v0=None,
+                            g_m=None, device=False):
+    """L = sum m |r(T)|^2 / sum m and its gradient (L, g_r0, g_v0, g_m)."""
+    if not device:
+        m, r0, v0 = (np.ascontiguousarray(x, np.float64) for x in (m, r0, v0))
+        n = m.shape[0]
+        loss = np.zeros(1) if loss is None else loss
+        g_r0 = np.zeros((n, 3)) if g_r0 is None else g_r0
+        g_v0 = np.zeros((n, 3)) if g_v0 is None else g_v0
+        g_m = np.zeros(n) if g_m is None else g_m
+    n = m.shape[0]
+    _check(lib().tsbts_adjoint_loss_grad(
+        ctx, *_ptrs((m, r0, v0, loss, g_r0, g_v0, g_m), n, device),
+        int(device)), ctx)
+    return (float(loss[0]) if not device else loss), g_r0, g_v0, g_m
+
+
+def tsbts_adjoint_get_stats(ctx) -> dict:
+    st = tsbts_adjoint_stats()
+    _check(lib().tsbts_adjoint_get_stats(ctx, C.byref(st)), ctx)
+    return st.as_dict()
+
+
 # --- convenience wrapper --------------------------------------------------
 
 class Simulation:
@@ -393,3 +519,58 @@ class Ensemble(Simulation):
 
     def cluster_energy(self):
         return tsbts_ensemble_energy(self.ctx, self.n_clusters)
+
+
+class Adjoint:
+    """Adjoint of a frozen block schedule (tsbts_adjoint_*): replay of the
+    schedule from (m, r0, v0) and reverse-mode gradients.
+
+    schedule = (step_tau, step_off, act) as from final_pass_schedule.
+    checkpoint_every = 0 tapes every step; K > 0 keeps a checkpoint every
+    K steps and recomputes during the reverse sweep."""
+
+    def __init__(self, n, eps, schedule, *, precision=TSBTS_FP64, k_max=20,
+                 checkpoint_every=0, exact_order=-1, device=0, stream=None):
+        cfg = tsbts_config_default()
+        cfg.precision = precision
+        cfg.k_max = k_max
+        cfg.exact_order = exact_order
+        cfg.device = device
+        cfg.stream = stream
+        self.n = int(n)
+        self.ctx = tsbts_create(cfg)
+        try:
+            tsbts_adjoint_init(self.ctx, n, eps, schedule, checkpoint_every)
+        except Exception:
+            tsbts_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def forward(self, m, r0, v0):
+        return tsbts_adjoint_forward(self.ctx, m, r0, v0)
+
+    def vjp(self, gr_T, gv_T=None):
+        return tsbts_adjoint_vjp(self.ctx, gr_T, gv_T, n=self.n)
+
+    def loss_grad(self, m, r0, v0):
+        return tsbts_adjoint_loss_grad(self.ctx, m, r0, v0)
+
+    def stats(self):
+        return tsbts_adjoint_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            tsbts_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
