@@ -14,6 +14,8 @@ JSON line keys beyond the driver contract:
   accuracy      relative energy errors of the GPU paths and the oracle on
                 the sample interval (bar: GPU <= 2x oracle)
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Other modes: --force-sweep (force kernel alone), --ensemble (512 clusters),
+--adjoint (gradient through a frozen block schedule, Plummer n = 8192).
 """
 from __future__ import annotations
 
@@ -325,6 +327,157 @@ def ensemble_bench(args):
     return 0
 
 
+def adjoint_bench(args):
+    """Gradient of the mass-weighted mean-square radius at the end of one
+    era with respect to the initial positions, velocities and masses,
+    through the era's final-pass block schedule (replay with Eq. 2
+    prediction, Eq. 3 forces, Eq. 1 correction, then reverse mode).
+    Plummer n = 8192, eps = 0.01, eta = 0.01, fixed era 0..1/4, three
+    passes; the schedule comes from the mixed integrator. One step = one
+    gradient (forward replay + reverse sweep) from device-resident inputs.
+    Pair terms counted per gradient: (E + n) n for the forward replay
+    (E = schedule entries, n^2 for the initial force) and 2 (E + n) n for
+    the two-sided force vector-Jacobian product."""
+    import numpy as np
+    import torch
+
+    from paper_1205_2288_gb300 import inputs, tsbts
+
+    n, eps, t_era = 8192, 0.01, 0.25
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    m, r, v = inputs.plummer(n, SEED)
+    sim = tsbts.Simulation(m, r, v, eps=eps, eta=ETA, dt_max=DT_MAX,
+                           n_iter=N_ITER, era_mode=0, era_log2=2,
+                           precision=tsbts.TSBTS_MIXED)
+    sim.schedule_log(40_000_000)
+    sim.step_era(t_era)
+    sched = tsbts.final_pass_schedule(sim.schedule(), 0)
+    sim.close()
+    E = int(sched[1][-1])
+    S = int(len(sched[0]))
+    pairs = 3 * (E + n) * n
+    dm, dr, dv = (torch.from_numpy(x).to(dev) for x in (m, r, v))
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    g = [torch.empty((n, 3), dtype=torch.float64, device=dev),
+         torch.empty((n, 3), dtype=torch.float64, device=dev),
+         torch.empty((n,), dtype=torch.float64, device=dev)]
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    variants = [("mixed_taped", tsbts.TSBTS_MIXED, 0),
+                ("mixed_checkpoint64", tsbts.TSBTS_MIXED, 64)]
+    if not args.no_fp64:
+        variants.append(("fp64_taped", tsbts.TSBTS_FP64, 0))
+    results = {}
+    sampler = ClockSampler(0)
+    clocks = None
+    for name, prec, K in variants:
+        adj = tsbts.Adjoint(n, eps, sched, precision=prec,
+                            checkpoint_every=K, exact_order=0,
+                            stream=stream.cuda_stream)
+        reps = args.steps if prec == tsbts.TSBTS_MIXED else 1
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup if prec == tsbts.TSBTS_MIXED else 1):
+                tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *g,
+                                              device=True)
+            torch.cuda.synchronize()
+            if name == "mixed_taped":
+                sampler.start()
+            ms = 0.0
+            fwd = bwd = 0.0
+            launches0 = adj.stats()["kernel_launches"]
+            for _ in range(reps):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *g,
+                                              device=True)
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                st = adj.stats()
+                fwd += st["forward_ms"]
+                bwd += st["backward_ms"]
+            if name == "mixed_taped":
+                clocks = sampler.stop()
+        assert torch.isfinite(g[0]).all()
+        ms /= reps
+        results[name] = {
+            "ms_per_gradient": ms, "Gpairs_s": pairs / (ms / 1e3) / 1e9,
+            "forward_ms": fwd / reps, "backward_ms": bwd / reps,
+            "pairs_backward_counted": st["pairs_backward"],
+            "device_bytes": st["device_bytes"],
+            "tape_bytes": st["tape_bytes"],
+            "checkpoint_bytes": st["checkpoint_bytes"],
+            "kernel_launches_per_gradient":
+                (st["kernel_launches"] - launches0) // reps}
+        adj.close()
+    head = results["mixed_taped"]
+    # end to end through the host-pointer API (copies in the timed region)
+    adj = tsbts.Adjoint(n, eps, sched, precision=tsbts.TSBTS_MIXED)
+    pin = [torch.from_numpy(x).pin_memory().numpy() for x in (m, r, v)]
+    outs = [np.zeros(1), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)]
+    adj.loss_grad(*pin)
+    t0 = time.perf_counter()
+    e2e_reps = max(1, min(args.steps, 2))
+    for _ in range(e2e_reps):
+        tsbts.tsbts_adjoint_loss_grad(adj.ctx, *pin, *outs)
+    e2e_s = (time.perf_counter() - t0) / e2e_reps
+    adj.close()
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2070e6 / OPS_PER_INTERACTION
+    bwd_pairs = 2 * (E + n) * n
+    achieved = bwd_pairs / (head["backward_ms"] / 1e3)
+    line = {
+        "metric": "adjoint: gradients/s of the era-end loss through the "
+                  "frozen final-pass schedule (G pair terms/s)",
+        "value": 1e3 / head["ms_per_gradient"], "unit": "gradients/s",
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["ms_per_gradient"], "higher_is_better": True,
+        "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "adjoint_plummer8192_eps0.01_eta0.01_era0-0.25"
+                               "_3iter_final_pass",
+                   "n": n, "eps": eps, "eta": ETA, "dt_max": DT_MAX,
+                   "era": "fixed 1/4", "n_iter": N_ITER,
+                   "schedule_steps": S, "schedule_entries": E,
+                   "loss": "sum m |r_T|^2 / sum m",
+                   "l2": "256 MiB buffer written between timed gradients"},
+        "pairs_per_gradient": pairs,
+        "Gpairs_s": head["Gpairs_s"],
+        "variants": results,
+        "gpu_launches": head["kernel_launches_per_gradient"] * args.steps,
+        "e2e": {"value": 1.0 / e2e_s, "unit": "gradients/s",
+                "h2d_bytes_per_step": 7 * 8 * n,
+                "d2h_bytes_per_step": (1 + 7 * n) * 8},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9,
+                     "peak": peak / 1e9, "unit": "Gpairs/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "reverse sweep (adj_back_prep + adj_vjp + "
+                               "adj_back_finalize)",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2070 MHz / "
+                                   "20 FMA-pipe ops per pair term"},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        oracle.set_threads(threads)
+        tau, off, act = sched
+        s_pre = int(np.searchsorted(off, 400_000))
+        pre = (tau[:s_pre], off[:s_pre + 1], act[:off[s_pre]])
+        e_pre = int(off[s_pre])
+        t0 = time.perf_counter()
+        oracle.loss_grad(m, r, v, eps, 20, pre)
+        osec = time.perf_counter() - t0
+        opairs = 3 * (e_pre + n) * n
+        line["cpu_baseline"] = {
+            "value": opairs / osec / 1e9, "unit": "Gpairs/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"first {s_pre} steps ({e_pre} entries) of the "
+                      f"schedule, one gradient, {osec:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,11 +494,15 @@ def main():
     ap.add_argument("--ensemble", action="store_true",
                     help="integrate the 512-cluster ensemble instead")
     ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="gradient through a frozen block schedule")
     args = ap.parse_args()
     if args.force_sweep:
         return force_sweep(args)
     if args.ensemble:
         return ensemble_bench(args)
+    if args.adjoint:
+        return adjoint_bench(args)
     ws, rank, local = dist_env()
     dist = init_dist(ws)
     if args.impl == "reference":

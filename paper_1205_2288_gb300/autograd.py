@@ -24,13 +24,21 @@ from . import tsbts
 
 def make_adjoint(n, eps, schedule, *, precision=tsbts.TSBTS_FP64, k_max=20,
                  checkpoint_every=0, device=0):
-    """An Adjoint on torch's current stream of `device`."""
-    stream = torch.cuda.current_stream(device).cuda_stream
+    """An Adjoint running on its own torch stream of `device`; every call
+    first waits for the caller's current stream, and returns once its
+    results are written."""
+    stream = torch.cuda.Stream(device=device)
     adj = tsbts.Adjoint(n, eps, schedule, precision=precision, k_max=k_max,
                         checkpoint_every=checkpoint_every, device=device,
-                        stream=stream)
+                        stream=stream.cuda_stream)
+    adj.torch_stream = stream
     adj.generation = 0
     return adj
+
+
+def _order(adj, t):
+    """Make the adjoint's stream wait for the work queued on t's device."""
+    adj.torch_stream.wait_stream(torch.cuda.current_stream(t.device))
 
 
 def _check_inputs(*ts):
@@ -46,6 +54,7 @@ class _Replay(torch.autograd.Function):
         r0, v0, m = r0.contiguous(), v0.contiguous(), m.contiguous()
         r_T = torch.empty_like(r0)
         v_T = torch.empty_like(v0)
+        _order(adj, r0)
         tsbts.tsbts_adjoint_forward(adj.ctx, m, r0, v0, r_T, v_T, device=True)
         adj.generation += 1
         ctx.adj = adj
@@ -59,6 +68,7 @@ class _Replay(torch.autograd.Function):
         if adj.generation != ctx.generation:
             # another forward ran since: replay these inputs again
             r0, v0, m = ctx.saved_tensors
+            _order(adj, r0)
             tsbts.tsbts_adjoint_forward(adj.ctx, m, r0, v0, None, None,
                                         device=True)
             adj.generation += 1
@@ -70,6 +80,7 @@ class _Replay(torch.autograd.Function):
         g_m = torch.empty((n,), dtype=torch.float64, device=dev)
         gr = None if gr_T is None else gr_T.contiguous()
         gv = None if gv_T is None else gv_T.contiguous()
+        _order(adj, g_r0)
         tsbts.tsbts_adjoint_vjp(adj.ctx, gr, gv, g_r0, g_v0, g_m, device=True,
                                 n=n)
         return g_r0, g_v0, g_m, None
@@ -85,6 +96,7 @@ class _EraLoss(torch.autograd.Function):
         g_r0 = torch.empty((n, 3), dtype=torch.float64, device=r0.device)
         g_v0 = torch.empty((n, 3), dtype=torch.float64, device=r0.device)
         g_m = torch.empty((n,), dtype=torch.float64, device=r0.device)
+        _order(adj, r0)
         tsbts.tsbts_adjoint_loss_grad(adj.ctx, m, r0, v0, loss, g_r0, g_v0,
                                       g_m, device=True)
         adj.generation += 1

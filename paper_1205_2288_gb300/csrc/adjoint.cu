@@ -11,6 +11,7 @@
 // full-state checkpoints every K steps. With checkpointing the reverse
 // sweep recomputes each segment's forward steps from its checkpoint.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -43,24 +44,27 @@ struct AdjCtx {
   // device
   int* act = nullptr;           // E
   long long* prev_e = nullptr;  // E: the same body's previous entry or -1
+  long long* next_e = nullptr;  // E: its next entry, or LLONG_MAX
   long long* last_e = nullptr;  // n: each body's last entry or -1
-  long long* cur_e = nullptr;   // n
+  long long* first_e = nullptr; // n: each body's first entry or LLONG_MAX
+  long long* cur_e = nullptr;   // n: reverse cursor
+  long long* fwd_e = nullptr;   // n: forward cursor
   int* iota = nullptr;          // n
   double* m = nullptr;
   double* io = nullptr;         // 7 n doubles: host inputs / outputs
   AdjState St{};
   std::vector<AdjState> ckpt;
+  std::vector<long long*> ckpt_fwd;  // forward cursor at each checkpoint
   AdjState fin{};  // final state of the forward replay (taped mode)
   AdjTape Tp{};
   AdjPred P{};
-  AdjSlots Sl{};
+  AdjSlots Sl[2]{};  // slots of even and odd steps (step -1: initial)
+  VjpOut O{};
   AdjCot C{};
   float4* jv = nullptr;         // zero velocities for the force kernel
   double* part = nullptr;
   long long part_cap = 0;
   int* nsplit = nullptr;
-  double* part_i = nullptr;
-  double* part_j = nullptr;
   int* err = nullptr;
   double* loss = nullptr;       // L, sum m
   bool have_forward = false;
@@ -68,6 +72,9 @@ struct AdjCtx {
   long long pairs_fwd = 0, pairs_bwd = 0, launches = 0;
   double fwd_ms = 0, bwd_ms = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // captured forward replay [0] and reverse sweep [1], and their kernels
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_kernels[2] = {0, 0};
 };
 
 }  // namespace tsbts
@@ -110,6 +117,8 @@ void copy_state(const AdjState& dst, const AdjState& src, int n,
 void adj_free(tsbts_ctx* c) {
   if (!c->adj) return;
   if (c->s) cudaStreamSynchronize(c->s);
+  for (cudaGraphExec_t g : c->adj->graph)
+    if (g) cudaGraphExecDestroy(g);
   free_list(c->adj->allocs);
   for (cudaEvent_t e : c->adj->ev)
     if (e) cudaEventDestroy(e);
@@ -145,8 +154,15 @@ ForceArgs force_args(const AdjCtx& A) {
   return fa;
 }
 
+// the force on the active bodies of a step: the lean mixed replay kernel
+// (sums into A.O.f), or the integrator's FP64 force kernel (ascending-j
+// sums in exact mode; partials summed by the correction kernel)
 void launch_step_force(tsbts_ctx* c, AdjCtx& A, const int* idx, int n_act,
-                       const Plan& plan) {
+                       const Plan& plan, const VjpSide& si) {
+  if (A.mixed) {
+    launch_adj_force(A.n, n_act, idx, A.eps * A.eps, A.P, si, A.O, c->s);
+    return;
+  }
   ForceArgs fa = force_args(A);
   fa.idx = idx;
   fa.n_act_fixed = n_act;
@@ -154,55 +170,101 @@ void launch_step_force(tsbts_ctx* c, AdjCtx& A, const int* idx, int n_act,
   ck(launch_force(A.mixed, fa, A.fl, c->s), "replay force");
 }
 
-// forward plans for every step, measured for the mixed path when a tuned
-// table exists for (device, n)
-void choose_plans(tsbts_ctx* c, AdjCtx& A) {
-  const std::vector<Plan>* tp =
-      A.mixed && A.n <= (1 << 20) ? tuned_plans(c->cfg.device, A.n, A.fl.grid)
-                                  : nullptr;
-  auto pick = [&](int na) {
-    Plan p = plan_force(A.mixed, A.exact, na, A.n, A.fl.grid, A.part_cap);
-    if (tp && (long long)(*tp)[na].S * 5 * na <= A.part_cap) p = (*tp)[na];
-    return p;
-  };
-  A.plan_init = pick(A.n);
-  for (long long s = 0; s < A.S; ++s)
-    A.plans[s] = pick((int)(A.off[s + 1] - A.off[s]));
+// accelerations of the force launch: A.O.f (mixed) or none (partials)
+double* const* fsum_of(AdjCtx& A) {
+  static double* const none[3] = {nullptr, nullptr, nullptr};
+  return A.mixed ? A.O.f : none;
 }
 
-// Replay steps [s0, s1) from the current state; with a tape, record the
-// pre-step state of their entries. Checkpoint k is saved before step k K.
+// plans of the FP64 force kernel for every step (the mixed replay uses its
+// own kernel and the reverse sweep's work splits)
+void choose_plans(tsbts_ctx* c, AdjCtx& A) {
+  (void)c;
+  A.plan_init = plan_force(A.mixed, A.exact, A.n, A.n, A.fl.grid, A.part_cap);
+  for (long long s = 0; s < A.S; ++s)
+    A.plans[s] = plan_force(A.mixed, A.exact, (int)(A.off[s + 1] - A.off[s]),
+                            A.n, A.fl.grid, A.part_cap);
+}
+
+// Replay steps [s0, s1) from the current state (bodies already predicted
+// to the block time of step s0); with a tape, record the pre-step state of
+// their entries. With save_ckpt, checkpoint k (state and forward cursor)
+// is saved before step k K.
 void replay_steps(tsbts_ctx* c, AdjCtx& A, long long s0, long long s1,
                   const AdjTape& tape, bool save_ckpt) {
   for (long long s = s0; s < s1; ++s) {
     if (save_ckpt && A.K > 0 && s % A.K == 0) {
       copy_state(A.ckpt[s / A.K], A.St, A.n, c->s);
+      ck(cudaMemcpyAsync(A.ckpt_fwd[s / A.K], A.fwd_e,
+                         sizeof(long long) * (size_t)A.n,
+                         cudaMemcpyDeviceToDevice, c->s),
+         "checkpoint copy");
     }
     const long long T = A.tau[s];
     const int na = (int)(A.off[s + 1] - A.off[s]);
-    const int* idx = A.act + A.off[s];
-    launch_adj_predict(A.n, T, A.inv_ticks, A.mixed, A.St, A.P, c->s);
-    launch_step_force(c, A, idx, na, A.plans[s]);
-    launch_adj_correct(na, idx, T, A.inv_ticks, A.part, A.nsplit, A.St, A.P,
-                       tape, A.off[s], A.err, c->s);
-    A.launches += 3;
+    launch_step_force(c, A, A.act + A.off[s], na, A.plans[s], A.shapes[s].si);
+    launch_adj_correct_predict(A.n, na, T, A.off[s], A.off[s + 1],
+                               s + 1 < s1 ? A.tau[s + 1] : -1, A.inv_ticks,
+                               A.mixed, A.part, A.nsplit, fsum_of(A), A.St,
+                               A.P, tape, A.fwd_e, A.next_e, A.err, c->s);
+    A.launches += 2;
   }
   ck(cudaGetLastError(), "replay launches");
 }
 
-void reverse_steps(tsbts_ctx* c, AdjCtx& A, long long s1, long long s0) {
+AdjBackPrep start_of(const AdjCtx& A, long long s) {
+  AdjBackPrep R{};
+  R.active = 1;
+  if (s < 0) {  // the initial force
+    R.all = 1;
+    R.T = 0;
+    R.e_lo = 0;
+    R.Sl = A.Sl[1];
+  } else {
+    R.T = A.tau[s];
+    R.e_lo = A.off[s];
+    R.Sl = A.Sl[s & 1];
+  }
+  return R;
+}
+
+AdjBackFin end_of(const AdjCtx& A, long long s) {
+  AdjBackFin F{};
+  F.active = 1;
+  F.T = s < 0 ? 0 : A.tau[s];
+  F.Sl = A.Sl[s < 0 ? 1 : (s & 1)];
+  return F;
+}
+
+void back_step(tsbts_ctx* c, AdjCtx& A, const AdjBackFin& F,
+               const AdjBackPrep& R) {
+  launch_adj_back_step(A.n, A.inv_ticks, A.mixed, F, R, A.St, A.Tp, A.cur_e,
+                       A.prev_e, A.C, A.P, A.O, A.err, c->s);
+  A.launches += 1;
+}
+
+void vjp_of(tsbts_ctx* c, AdjCtx& A, long long s) {
   const double eps2 = A.eps * A.eps;
+  if (s < 0)
+    launch_adj_vjp(A.mixed, A.n, A.n, A.iota, eps2, A.P, A.Sl[1],
+                   A.shape_init, A.O, c->s);
+  else
+    launch_adj_vjp(A.mixed, A.n, (int)(A.off[s + 1] - A.off[s]),
+                   A.act + A.off[s], eps2, A.P, A.Sl[s & 1], A.shapes[s], A.O,
+                   c->s);
+  A.launches += 1;
+}
+
+// Reverse steps s1 - 1 down to s0, whose tape is loaded; step s0 - 1 is
+// started too when it needs no tape (the initial force, s0 = 0).
+void reverse_steps(tsbts_ctx* c, AdjCtx& A, long long s1, long long s0) {
+  const AdjBackFin none_f{};
+  AdjBackPrep none_r{};
+  back_step(c, A, none_f, start_of(A, s1 - 1));
   for (long long s = s1 - 1; s >= s0; --s) {
-    const long long T = A.tau[s];
-    const int na = (int)(A.off[s + 1] - A.off[s]);
-    launch_adj_back_prep(A.n, T, A.inv_ticks, A.off[s], 0, A.mixed, A.St,
-                         A.Tp, A.cur_e, A.prev_e, A.C, A.P, A.Sl, c->s);
-    launch_adj_vjp(A.mixed, A.n, na, A.act + A.off[s], eps2, A.P, A.Sl,
-                   A.shapes[s], A.part_i, A.part_j, c->s);
-    launch_adj_back_finalize(A.n, na, T, A.inv_ticks, A.shapes[s], A.part_i,
-                             A.part_j, A.P, A.Sl, A.St, A.C, A.err, c->s);
-    A.launches += 3;
-    A.pairs_bwd += 2LL * na * A.n;
+    vjp_of(c, A, s);
+    back_step(c, A, end_of(A, s),
+              s > s0 || s0 == 0 ? start_of(A, s - 1) : none_r);
   }
   ck(cudaGetLastError(), "reverse launches");
 }
@@ -215,40 +277,28 @@ void check_err(tsbts_ctx* c, AdjCtx& A, const char* what, int* rc) {
   if (e) *rc = fail(c, TSBTS_ERR_NONFINITE, what);
 }
 
-// forward replay from inputs on the device (AoS)
-int forward_impl(tsbts_ctx* c, AdjCtx& A, const double* dm, const double* dr,
-                 const double* dv) {
-  ck(cudaMemsetAsync(A.err, 0, sizeof(int), c->s), "memset");
-  ck(cudaEventRecord(A.ev[0], c->s), "event");
-  launch_adj_load(A.n, dm, dr, dv, A.mixed, A.m, A.St, A.P, A.err, c->s);
-  ForceArgs fa = force_args(A);
-  fa.idx = A.iota;
-  fa.n_act_fixed = A.n;
-  fa.plan = A.plan_init;
-  ck(launch_force(A.mixed, fa, A.fl, c->s), "initial force");
-  launch_adj_init_accel(A.n, A.part, A.nsplit, A.St, A.err, c->s);
+// All work of the forward replay, inputs read from A.io (m, r0, v0).
+void enqueue_forward(tsbts_ctx* c, AdjCtx& A) {
+  const size_t n = (size_t)A.n;
+  launch_adj_load(A.n, A.io, A.io + n, A.io + 4 * n, A.mixed, A.m, A.St, A.P,
+                  A.err, c->s);
+  launch_step_force(c, A, A.iota, A.n, A.plan_init, A.shape_init.si);
+  launch_adj_init_accel(A.n, A.part, A.nsplit, fsum_of(A),
+                        A.S > 0 ? A.tau[0] : -1, A.inv_ticks, A.mixed, A.St,
+                        A.P, A.err, c->s);
+  ck(cudaMemcpyAsync(A.fwd_e, A.first_e, sizeof(long long) * n,
+                     cudaMemcpyDeviceToDevice, c->s),
+     "copy entry cursors");
   A.launches += 3;
   AdjTape none{};
   replay_steps(c, A, 0, A.S, A.K == 0 ? A.Tp : none, true);
   // the taped reverse sweep starts from the final state; keep it so that
   // every sweep of this forward replay can start there
   if (A.K == 0) copy_state(A.fin, A.St, A.n, c->s);
-  ck(cudaEventRecord(A.ev[1], c->s), "event");
-  int rc = TSBTS_OK;
-  check_err(c, A, "non-finite input or force in the replay", &rc);
-  float ms = 0;
-  ck(cudaEventElapsedTime(&ms, A.ev[0], A.ev[1]), "event time");
-  A.fwd_ms = ms;
-  A.pairs_fwd = (long long)A.n * A.n + A.E * (long long)A.n;
-  A.have_forward = rc == TSBTS_OK;
-  return rc;
 }
 
-// reverse sweep from the seeds already in A.C
-int backward_impl(tsbts_ctx* c, AdjCtx& A) {
-  ck(cudaMemsetAsync(A.err, 0, sizeof(int), c->s), "memset");
-  ck(cudaEventRecord(A.ev[0], c->s), "event");
-  A.pairs_bwd = 0;
+// All work of the reverse sweep, from the seeds already in A.C.
+void enqueue_backward(tsbts_ctx* c, AdjCtx& A) {
   ck(cudaMemcpyAsync(A.cur_e, A.last_e, sizeof(long long) * (size_t)A.n,
                      cudaMemcpyDeviceToDevice, c->s),
      "copy entry cursors");
@@ -259,32 +309,89 @@ int backward_impl(tsbts_ctx* c, AdjCtx& A) {
     for (long long g = A.n_ckpt - 1; g >= 0; --g) {
       const long long s0 = g * A.K, s1 = std::min(A.S, s0 + A.K);
       copy_state(A.St, A.ckpt[g], A.n, c->s);
+      ck(cudaMemcpyAsync(A.fwd_e, A.ckpt_fwd[g],
+                         sizeof(long long) * (size_t)A.n,
+                         cudaMemcpyDeviceToDevice, c->s),
+         "checkpoint copy");
+      launch_adj_predict(A.n, A.tau[s0], A.inv_ticks, A.mixed, A.St, A.P,
+                         c->s);
+      A.launches += 1;
       AdjTape tape = A.Tp;
       tape.base = A.off[s0];
       replay_steps(c, A, s0, s1, tape, false);
-      A.pairs_bwd += (A.off[s1] - A.off[s0]) * (long long)A.n;
       A.Tp.base = tape.base;
       reverse_steps(c, A, s1, s0);
     }
     A.Tp.base = 0;
   }
-  // the initial force a0 = f(r0): every body active at tick 0
-  const double eps2 = A.eps * A.eps;
-  launch_adj_back_prep(A.n, 0, A.inv_ticks, 0, 1, A.mixed, A.St, A.Tp,
-                       A.cur_e, A.prev_e, A.C, A.P, A.Sl, c->s);
-  launch_adj_vjp(A.mixed, A.n, A.n, A.iota, eps2, A.P, A.Sl, A.shape_init,
-                 A.part_i, A.part_j, c->s);
-  launch_adj_back_finalize(A.n, A.n, 0, A.inv_ticks, A.shape_init, A.part_i,
-                           A.part_j, A.P, A.Sl, A.St, A.C, A.err, c->s);
-  A.launches += 3;
-  A.pairs_bwd += 2LL * A.n * A.n;
+  // the initial force a0 = f(r0) (started by the last reverse step)
+  vjp_of(c, A, -1);
+  back_step(c, A, end_of(A, -1), AdjBackPrep{});
   ck(cudaGetLastError(), "reverse launches");
+}
+
+// Run the work of `enq` on the stream: directly (graph_steps == 0), or by
+// replaying its CUDA graph, captured at the first call (the schedule, the
+// plans and every buffer address are fixed for the life of the adjoint).
+void run_work(tsbts_ctx* c, AdjCtx& A, int which,
+              void (*enq)(tsbts_ctx*, AdjCtx&)) {
+  if (c->cfg.graph_steps == 0) {
+    enq(c, A);
+    return;
+  }
+  cudaGraphExec_t& exec = A.graph[which];
+  if (!exec) {
+    const long long l0 = A.launches;
+    cudaGraph_t g;
+    ck(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal),
+       "begin capture");
+    try {
+      enq(c, A);
+    } catch (...) {
+      cudaStreamEndCapture(c->s, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    ck(cudaStreamEndCapture(c->s, &g), "end capture");
+    const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    ck(e, "graph instantiate");
+    A.graph_kernels[which] = A.launches - l0;
+    A.launches = l0;
+  }
+  ck(cudaGraphLaunch(exec, c->s), "graph launch");
+  A.launches += A.graph_kernels[which];
+}
+
+int forward_impl(tsbts_ctx* c, AdjCtx& A) {
+  ck(cudaMemsetAsync(A.err, 0, sizeof(int), c->s), "memset");
+  ck(cudaEventRecord(A.ev[0], c->s), "event");
+  run_work(c, A, 0, enqueue_forward);
+  ck(cudaEventRecord(A.ev[1], c->s), "event");
+  int rc = TSBTS_OK;
+  check_err(c, A, "non-finite input or force in the replay", &rc);
+  float ms = 0;
+  ck(cudaEventElapsedTime(&ms, A.ev[0], A.ev[1]), "event time");
+  A.fwd_ms = ms;
+  A.pairs_fwd = (A.E + A.n) * (long long)A.n;
+  A.have_forward = rc == TSBTS_OK;
+  return rc;
+}
+
+int backward_impl(tsbts_ctx* c, AdjCtx& A) {
+  ck(cudaMemsetAsync(A.err, 0, sizeof(int), c->s), "memset");
+  ck(cudaEventRecord(A.ev[0], c->s), "event");
+  run_work(c, A, 1, enqueue_backward);
   ck(cudaEventRecord(A.ev[1], c->s), "event");
   int rc = TSBTS_OK;
   check_err(c, A, "non-finite cotangent in the reverse sweep", &rc);
   float ms = 0;
   ck(cudaEventElapsedTime(&ms, A.ev[0], A.ev[1]), "event time");
   A.bwd_ms = ms;
+  // two-sided force VJP of every step and of the initial force, plus the
+  // forward steps recomputed from checkpoints
+  A.pairs_bwd = 2 * (A.E + A.n) * (long long)A.n +
+                (A.K > 0 ? A.E * (long long)A.n : 0);
   return rc;
 }
 
@@ -301,26 +408,18 @@ void to_out(tsbts_ctx* c, AdjCtx& A, double* const src[3], double* dst,
   ck(cudaStreamSynchronize(c->s), "synchronize");
 }
 
-// inputs on the device: host arrays are staged through A.io
+// inputs into A.io (m, r0, v0), from host or device arrays; the replay
+// always reads them there, so a captured graph serves every call
 void stage_in(tsbts_ctx* c, AdjCtx& A, const double* m, const double* r,
-              const double* v, bool dev, const double** dm, const double** dr,
-              const double** dv) {
-  if (dev) {
-    *dm = m;
-    *dr = r;
-    *dv = v;
-    return;
-  }
+              const double* v, bool dev) {
   const size_t n = (size_t)A.n;
-  ck(cudaMemcpyAsync(A.io, m, sizeof(double) * n, cudaMemcpyHostToDevice,
-                     c->s), "copy m");
-  ck(cudaMemcpyAsync(A.io + n, r, sizeof(double) * 3 * n,
-                     cudaMemcpyHostToDevice, c->s), "copy r");
-  ck(cudaMemcpyAsync(A.io + 4 * n, v, sizeof(double) * 3 * n,
-                     cudaMemcpyHostToDevice, c->s), "copy v");
-  *dm = A.io;
-  *dr = A.io + n;
-  *dv = A.io + 4 * n;
+  const cudaMemcpyKind kind =
+      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  ck(cudaMemcpyAsync(A.io, m, sizeof(double) * n, kind, c->s), "copy m");
+  ck(cudaMemcpyAsync(A.io + n, r, sizeof(double) * 3 * n, kind, c->s),
+     "copy r");
+  ck(cudaMemcpyAsync(A.io + 4 * n, v, sizeof(double) * 3 * n, kind, c->s),
+     "copy v");
 }
 
 }  // namespace
@@ -385,19 +484,26 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     A.off.assign(step_off, step_off + n_steps + 1);
     if (n_steps == 0) A.off.assign(1, 0);
     A.fl = force_launch_shape(A.mixed, ctx->cfg.device);
-    // entry links: previous entry of the same body, last entry per body
-    std::vector<long long> prev((size_t)std::max<long long>(E, 1), -1),
-        last((size_t)n, -1);
+    // entry links: the same body's previous and next entries, and each
+    // body's first and last entries
+    const size_t e1 = (size_t)std::max<long long>(E, 1);
+    std::vector<long long> prev(e1, -1), next(e1, LLONG_MAX),
+        last((size_t)n, -1), first((size_t)n, LLONG_MAX);
     for (long long e = 0; e < E; ++e) {
       const int i = act[e];
       prev[e] = last[i];
+      if (last[i] >= 0) next[last[i]] = e;
+      if (first[i] == LLONG_MAX) first[i] = e;
       last[i] = e;
     }
     const int ni = (int)n;
     A.act = adj_alloc<int>(A, E);
     A.prev_e = adj_alloc<long long>(A, E);
+    A.next_e = adj_alloc<long long>(A, E);
     A.last_e = adj_alloc<long long>(A, ni);
+    A.first_e = adj_alloc<long long>(A, ni);
     A.cur_e = adj_alloc<long long>(A, ni);
+    A.fwd_e = adj_alloc<long long>(A, ni);
     A.iota = adj_alloc<int>(A, ni);
     std::vector<int> iota(ni);
     for (int k = 0; k < ni; ++k) iota[k] = k;
@@ -406,8 +512,12 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
                          ctx->s), "copy schedule");
       ck(cudaMemcpyAsync(A.prev_e, prev.data(), sizeof(long long) * E,
                          cudaMemcpyHostToDevice, ctx->s), "copy schedule");
+      ck(cudaMemcpyAsync(A.next_e, next.data(), sizeof(long long) * E,
+                         cudaMemcpyHostToDevice, ctx->s), "copy schedule");
     }
     ck(cudaMemcpyAsync(A.last_e, last.data(), sizeof(long long) * ni,
+                       cudaMemcpyHostToDevice, ctx->s), "copy schedule");
+    ck(cudaMemcpyAsync(A.first_e, first.data(), sizeof(long long) * ni,
                        cudaMemcpyHostToDevice, ctx->s), "copy schedule");
     ck(cudaMemcpyAsync(A.iota, iota.data(), sizeof(int) * ni,
                        cudaMemcpyHostToDevice, ctx->s), "copy iota");
@@ -416,12 +526,23 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     A.St = alloc_state(A, ni);
     for (int c = 0; c < 3; ++c) {
       A.P.p[c] = adj_alloc<double>(A, ni);
-      A.Sl.lam[c] = adj_alloc<double>(A, ni);
-      A.Sl.gp0[c] = adj_alloc<double>(A, ni);
-      A.Sl.ap[c] = adj_alloc<double>(A, ni);
       A.C.gr[c] = adj_alloc<double>(A, ni);
       A.C.gv[c] = adj_alloc<double>(A, ni);
       A.C.ga[c] = adj_alloc<double>(A, ni);
+      A.O.u[c] = adj_alloc<double>(A, ni);
+    }
+    for (int c = 0; c < 4; ++c) A.O.g[c] = adj_alloc<double>(A, ni);
+    for (int c = 0; c < 3; ++c) A.O.f[c] = adj_alloc<double>(A, ni);
+    for (AdjSlots& Sl : A.Sl) {
+      for (int c = 0; c < 3; ++c) {
+        Sl.lam[c] = adj_alloc<double>(A, ni);
+        Sl.gp0[c] = adj_alloc<double>(A, ni);
+        Sl.ap[c] = adj_alloc<double>(A, ni);
+      }
+      Sl.ahi = adj_alloc<float4>(A, ni);
+      Sl.alo = adj_alloc<float4>(A, ni);
+      Sl.alam = adj_alloc<float4>(A, ni);
+      Sl.slot = adj_alloc<int>(A, ni);
     }
     A.P.m = A.m;
     A.C.gm = adj_alloc<double>(A, ni);
@@ -429,10 +550,6 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     A.P.jlo = adj_alloc<float4>(A, ni);
     A.jv = adj_alloc<float4>(A, ni);
     ck(cudaMemsetAsync(A.jv, 0, sizeof(float4) * ni, ctx->s), "memset");
-    A.Sl.ahi = adj_alloc<float4>(A, ni);
-    A.Sl.alo = adj_alloc<float4>(A, ni);
-    A.Sl.alam = adj_alloc<float4>(A, ni);
-    A.Sl.slot = adj_alloc<int>(A, ni);
     A.part_cap = std::max<long long>(A.fl.part_cap, 5LL * ni);
     A.part = adj_alloc<double>(A, A.part_cap);
     A.nsplit = adj_alloc<int>(A, 1);
@@ -454,26 +571,37 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     A.Tp.base = 0;
     A.tape_bytes = A.bytes - before_tape;
     const long long before_ckpt = A.bytes;
-    for (long long g = 0; g < A.n_ckpt; ++g) A.ckpt.push_back(alloc_state(A, ni));
+    for (long long g = 0; g < A.n_ckpt; ++g) {
+      A.ckpt.push_back(alloc_state(A, ni));
+      A.ckpt_fwd.push_back(adj_alloc<long long>(A, ni));
+    }
     if (A.K == 0) A.fin = alloc_state(A, ni);
     A.ckpt_bytes = A.bytes - before_ckpt;
     // reverse work splits and their partial-sum buffers
     A.shapes.resize(A.S);
     A.plans.resize(A.S);
-    long long cap_i = 0, cap_j = 0;
-    auto need = [&](const VjpShape& v, long long na) {
-      cap_i = std::max(cap_i, (long long)v.si.S * 3 * na);
-      cap_j = std::max(cap_j, (long long)v.sj.S * 4 * ni);
+    long long cap_i = 0, cap_j = 0, grp_i = 0, grp_j = 0;
+    auto need = [&](const VjpShape& v) {
+      cap_i = std::max(cap_i, (long long)v.si.groups * v.si.S * 4 * 128 /
+                                  v.si.tpt);
+      cap_j = std::max(cap_j, (long long)v.sj.groups * v.sj.S * 4 * 128 /
+                                  v.sj.tpt);
+      grp_i = std::max<long long>(grp_i, v.si.groups);
+      grp_j = std::max<long long>(grp_j, v.sj.groups);
     };
     A.shape_init = vjp_shape(ni, ni, ctx->sms);
-    need(A.shape_init, ni);
+    need(A.shape_init);
     for (long long s = 0; s < A.S; ++s) {
       const int na = (int)(A.off[s + 1] - A.off[s]);
       A.shapes[s] = vjp_shape(ni, na, ctx->sms);
-      need(A.shapes[s], na);
+      need(A.shapes[s]);
     }
-    A.part_i = adj_alloc<double>(A, cap_i);
-    A.part_j = adj_alloc<double>(A, cap_j);
+    A.O.part_i = adj_alloc<double>(A, cap_i);
+    A.O.part_j = adj_alloc<double>(A, cap_j);
+    A.O.cnt_i = adj_alloc<int>(A, grp_i);
+    A.O.cnt_j = adj_alloc<int>(A, grp_j);
+    ck(cudaMemsetAsync(A.O.cnt_i, 0, sizeof(int) * grp_i, ctx->s), "memset");
+    ck(cudaMemsetAsync(A.O.cnt_j, 0, sizeof(int) * grp_j, ctx->s), "memset");
     choose_plans(ctx, A);
     ck(cudaEventCreate(&A.ev[0]), "event");
     ck(cudaEventCreate(&A.ev[1]), "event");
@@ -495,22 +623,8 @@ int tsbts_adjoint_forward(tsbts_ctx* ctx, const double* m, const double* r0,
   AdjCtx& A = *ctx->adj;
   try {
     ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
-    const double *dm, *dr, *dv;
-    stage_in(ctx, A, m, r0, v0, device_ptrs != 0, &dm, &dr, &dv);
-    if (A.mixed && A.n <= (1 << 20) &&
-        !tuned_plans(ctx->cfg.device, A.n, A.fl.grid)) {
-      // measured force plans for this n, timed on the initial positions
-      launch_adj_load(A.n, dm, dr, dv, A.mixed, A.m, A.St, A.P, A.err, ctx->s);
-      std::vector<Plan> t;
-      ForceArgs base = force_args(A);
-      base.idx = A.iota;
-      base.has_plan = 0;
-      ck(autotune_mixed_plans(ctx->cfg.device, base, A.fl, A.nsplit, ctx->s,
-                              &t),
-         "force plan autotuning");
-      choose_plans(ctx, A);
-    }
-    rc = forward_impl(ctx, A, dm, dr, dv);
+    stage_in(ctx, A, m, r0, v0, device_ptrs != 0);
+    rc = forward_impl(ctx, A);
     if (rc) return rc;
     to_out(ctx, A, A.St.r, r_T, device_ptrs != 0);
     to_out(ctx, A, A.St.v, v_T, device_ptrs != 0);

@@ -23,10 +23,12 @@
 // The FP64 replay uses the integrator's op-by-op FP64 expressions and force
 // kernels, so it reproduces a sequential FP64 replay bit for bit when the
 // force sums run in ascending j. The mixed pair terms of the reverse sweep
-// are FP32 on double-single relative coordinates, summed in FP32 over at
-// most kFold sources and then in FP64.
+// are FP32 on double-single relative coordinates, two sources per packed
+// f32x2 instruction, summed in FP32 over one shared-memory tile of sources
+// and then in FP64.
 #include <algorithm>
 
+#include "force_device.cuh"
 #include "tsbts_kernels.cuh"
 
 namespace tsbts {
@@ -34,7 +36,34 @@ namespace tsbts {
 namespace {
 
 constexpr int kAdjThreads = 128;
-constexpr int kFold = 64;  // FP32 pair terms per FP64 fold, per lane
+
+// tuning of the force vector-Jacobian product and the replay force
+// (compile-time; defaults measured on GB300): lanes per target, threads in
+// flight per SM that the split count aims at, most splits, sources per
+// shared-memory tile, unroll of the packed pair loop, register budget hint
+#ifndef TSBTS_VJP_TPT
+#define TSBTS_VJP_TPT 4
+#endif
+#ifndef TSBTS_VJP_WANT
+#define TSBTS_VJP_WANT 512
+#endif
+#ifndef TSBTS_VJP_SMAX
+#define TSBTS_VJP_SMAX 16
+#endif
+#ifndef TSBTS_VJP_TILE
+#define TSBTS_VJP_TILE 512
+#endif
+#ifndef TSBTS_VJP_UNROLL
+#define TSBTS_VJP_UNROLL 2
+#endif
+#ifndef TSBTS_VJP_MINB
+#define TSBTS_VJP_MINB 1
+#endif
+constexpr int kVjpTpt = TSBTS_VJP_TPT;
+constexpr int kVjpWant = TSBTS_VJP_WANT;
+constexpr int kVjpSmax = TSBTS_VJP_SMAX;
+constexpr int kVjpMinBlocks = TSBTS_VJP_MINB;
+constexpr int kVjpUnroll = TSBTS_VJP_UNROLL;
 
 __device__ __forceinline__ void pack_ds(double x, double y, double z, float w,
                                         float4& hi, float4& lo) {
@@ -112,17 +141,40 @@ __device__ __forceinline__ void partial_sum(const double* part, int n_act,
   }
 }
 
+// Initial accelerations (the force on every body at r0) and the Eq. 2
+// prediction of every body to the first block time T_next (< 0: none).
+// new accelerations of a step: from the replay force kernel's sums (F.f)
+// when given, else from the integrator force kernel's j-split partials
+struct FSum {
+  const double* f[3];
+};
+__device__ __forceinline__ void force_of(const FSum& F, const double* part,
+                                         int n_act, int S, int k,
+                                         double an[3]) {
+  if (F.f[0]) {
+    for (int c = 0; c < 3; ++c) an[c] = F.f[c][k];
+  } else {
+    partial_sum(part, n_act, S, k, an);
+  }
+}
+
 __global__ void adj_init_accel_kernel(int n, const double* part,
-                                      const int* nsplit, AdjState St,
+                                      const int* nsplit, FSum F,
+                                      long long T_next, double inv_ticks,
+                                      int mixed, AdjState St, AdjPred P,
                                       int* err) {
-  const int S = *nsplit;
+  const int S = F.f[0] ? 1 : *nsplit;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
     double an[3];
-    partial_sum(part, n, S, j, an);
+    force_of(F, part, n, S, j, an);
     if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]))
       atomicOr(err, 1);
     for (int c = 0; c < 3; ++c) St.a[c][j] = an[c];
+    if (T_next >= 0) {
+      double p[3];
+      predict_into(j, T_next, inv_ticks, mixed, St, P, p);
+    }
   }
 }
 
@@ -135,37 +187,89 @@ __global__ void adj_predict_kernel(int n, long long T, double inv_ticks,
   }
 }
 
-// Eq. 1 for the active bodies; the tape receives their pre-step state
-__global__ void adj_correct_kernel(int n_act, const int* idx, long long T,
-                                   double inv_ticks, const double* part,
-                                   const int* nsplit, AdjState St, AdjPred P,
-                                   AdjTape Tp, long long e0, int* err) {
-  const int S = *nsplit;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act;
-       k += gridDim.x * blockDim.x) {
-    const int i = idx[k];
-    double an[3];
-    partial_sum(part, n_act, S, k, an);
-    if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]))
-      atomicOr(err, 1);
-    if (Tp.tau) {
-      const long long t = e0 + k - Tp.base;
-      for (int c = 0; c < 3; ++c) {
-        Tp.x[c][t] = St.r[c][i];
-        Tp.x[3 + c][t] = St.v[c][i];
-        Tp.x[6 + c][t] = St.a[c][i];
-      }
-      Tp.tau[t] = St.tau[i];
-    }
-    const double h = tick_h(T, St.tau[i], inv_ticks);
+// The per-body kernels below are latency-bound: each body's loads are all
+// issued before any of its stores (the state and cotangent arrays are
+// reached through pointers the compiler must assume may alias), so that a
+// body waits for at most two dependent rounds of memory accesses.
+
+// packed j records of a predicted position
+__device__ __forceinline__ void store_pred(int j, const double p[3], float w,
+                                           int mixed, const AdjPred& P) {
+  for (int c = 0; c < 3; ++c) P.p[c][j] = p[c];
+  if (mixed) {
+    float4 hi, lo;
+    pack_ds(p[0], p[1], p[2], w, hi, lo);
+    P.jhi[j] = hi;
+    P.jlo[j] = lo;
+  }
+}
+
+// Per body: Eq. 1 if the body is active in the step [e_lo, e_hi) of the
+// schedule (fwd_e[j] is its next entry not yet replayed; the tape receives
+// its pre-step state), then Eq. 2 prediction to the next block time T_next
+// (< 0: none).
+__global__ void adj_correct_predict_kernel(
+    int n, int n_act, long long T, long long e_lo, long long e_hi,
+    long long T_next, double inv_ticks, int mixed, const double* part,
+    const int* nsplit, FSum F, AdjState St, AdjPred P, AdjTape Tp,
+    long long* fwd_e, const long long* next_e, int* err) {
+  const int S = F.f[0] ? 1 : *nsplit;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += gridDim.x * blockDim.x) {
+    // loads
+    const long long e = fwd_e[j];
+    long long tau = St.tau[j];
+    double r[3], v[3], a[3], p[3];
     for (int c = 0; c < 3; ++c) {
-      St.v[c][i] = __dadd_rn(
-          St.v[c][i],
-          __dmul_rn(__dmul_rn(0.5, __dadd_rn(St.a[c][i], an[c])), h));
-      St.r[c][i] = P.p[c][i];
-      St.a[c][i] = an[c];
+      r[c] = St.r[c][j];
+      v[c] = St.v[c][j];
+      a[c] = St.a[c][j];
+      p[c] = P.p[c][j];
     }
-    St.tau[i] = T;
+    const float mf = mixed ? (float)P.m[j] : 0.f;
+    const bool active = e < e_hi;
+    double an[3] = {0.0, 0.0, 0.0};
+    long long ne = 0;
+    if (active) {
+      force_of(F, part, n_act, S, (int)(e - e_lo), an);
+      ne = next_e[e];
+    }
+    if (active) {
+      if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]))
+        atomicOr(err, 1);
+      if (Tp.tau) {
+        const long long t = e - Tp.base;
+        for (int c = 0; c < 3; ++c) {
+          Tp.x[c][t] = r[c];
+          Tp.x[3 + c][t] = v[c];
+          Tp.x[6 + c][t] = a[c];
+        }
+        Tp.tau[t] = tau;
+      }
+      // Eq. 1 over the body's own step
+      const double h = tick_h(T, tau, inv_ticks);
+      for (int c = 0; c < 3; ++c) {
+        v[c] = __dadd_rn(v[c],
+                         __dmul_rn(__dmul_rn(0.5, __dadd_rn(a[c], an[c])), h));
+        r[c] = p[c];
+        a[c] = an[c];
+        St.r[c][j] = r[c];
+        St.v[c][j] = v[c];
+        St.a[c][j] = a[c];
+      }
+      tau = T;
+      St.tau[j] = T;
+      fwd_e[j] = ne;
+    }
+    if (T_next >= 0) {
+      const double h = tick_h(T_next, tau, inv_ticks);
+      double q[3];
+      for (int c = 0; c < 3; ++c) {
+        double vp;
+        taylor1(r[c], v[c], a[c], h, q[c], vp);
+      }
+      store_pred(j, q, mf, mixed, P);
+    }
   }
 }
 
@@ -173,74 +277,184 @@ __global__ void adj_correct_kernel(int n_act, const int* idx, long long T,
 // Reverse sweep
 // ---------------------------------------------------------------------
 
-// Per body: restore the pre-step state of the active bodies from the tape
-// (cur_e[j] is body j's latest entry not yet reversed), the Eq. 1 part of
-// the reverse step for them, and the Eq. 2 prediction of every body. With
-// `all` every body is active at T = 0 (the initial force): its cotangent
-// ga becomes lam and nothing is restored.
-__global__ void adj_back_prep_kernel(int n, long long T, double inv_ticks,
-                                     long long e_lo, int all, int mixed,
-                                     AdjState St, AdjTape Tp,
-                                     long long* cur_e, const long long* prev_e,
-                                     AdjCot C, AdjPred P, AdjSlots Sl) {
+// One kernel ends a reverse step and starts the step before it, body by
+// body (each body's two halves touch only its own state and cotangents;
+// the two steps use different slot arrays).
+//
+// End of the reverse step at block time F.T: the body's position cotangent
+// (m_j G_j from the j side; for a body active in slot k also the cotangent
+// of its new position minus u_k) passed through Eq. 2 to gr, gv, ga, and
+// its mass cotangent Z_j.
+//
+// Start of the reverse step at block time R.T: restore the pre-step state
+// of an active body from the tape (cur_e[j] is its latest entry not yet
+// reversed), the Eq. 1 part of the reverse step, and the Eq. 2 prediction.
+// With R.all every body is active at T = 0 (the initial force): its
+// cotangent ga becomes lam and nothing is restored.
+__global__ void adj_back_step_kernel(int n, double inv_ticks, int mixed,
+                                     AdjBackFin F, AdjBackPrep R, AdjState St,
+                                     AdjTape Tp, long long* cur_e,
+                                     const long long* prev_e, AdjCot C,
+                                     AdjPred P, VjpOut O, int* err) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
-    int k = -1;
-    if (all) {
-      k = j;
-    } else {
-      const long long e = cur_e[j];
-      if (e >= e_lo) {
-        k = (int)(e - e_lo);
+    // first round of loads
+    const long long tau0 = St.tau[j];
+    double gr[3], gv[3], ga[3];
+    for (int c = 0; c < 3; ++c) {
+      gr[c] = C.gr[c][j];
+      gv[c] = C.gv[c][j];
+      ga[c] = C.ga[c][j];
+    }
+    double gm = 0.0, G[4] = {0.0, 0.0, 0.0, 0.0}, mj = 0.0;
+    int kf = -1;
+    if (F.active) {
+      gm = C.gm[j];
+      kf = F.Sl.slot[j];
+      for (int c = 0; c < 4; ++c) G[c] = O.g[c][j];
+      mj = P.m[j];
+    }
+    long long e = -1;
+    double r[3], v[3], a[3];
+    long long tau1 = tau0;
+    float mf = 0.f;
+    if (R.active) {
+      if (!R.all) e = cur_e[j];
+      for (int c = 0; c < 3; ++c) {
+        r[c] = St.r[c][j];
+        v[c] = St.v[c][j];
+        a[c] = St.a[c][j];
+      }
+      if (mixed) mf = (float)P.m[j];
+    }
+    // second round: the slot's values and the tape
+    double gp0[3] = {0.0, 0.0, 0.0}, u[3] = {0.0, 0.0, 0.0};
+    if (kf >= 0)
+      for (int c = 0; c < 3; ++c) {
+        gp0[c] = F.Sl.gp0[c][kf];
+        u[c] = O.u[c][kf];
+      }
+    int kr = -1;
+    long long pe = 0;
+    if (R.active) {
+      if (R.all) {
+        kr = j;
+      } else if (e >= R.e_lo) {
+        kr = (int)(e - R.e_lo);
         const long long t = e - Tp.base;
         for (int c = 0; c < 3; ++c) {
-          St.r[c][j] = Tp.x[c][t];
-          St.v[c][j] = Tp.x[3 + c][t];
-          St.a[c][j] = Tp.x[6 + c][t];
+          r[c] = Tp.x[c][t];
+          v[c] = Tp.x[3 + c][t];
+          a[c] = Tp.x[6 + c][t];
         }
-        St.tau[j] = Tp.tau[t];
-        cur_e[j] = prev_e[e];
+        tau1 = Tp.tau[t];
+        pe = prev_e[e];
       }
     }
-    Sl.slot[j] = k;
-    double p[3];
-    predict_into(j, T, inv_ticks, mixed, St, P, p);
-    if (k < 0) continue;
-    const double h = tick_h(T, St.tau[j], inv_ticks);
-    const double hh = __dmul_rn(0.5, h);
-    double lam[3];
-    for (int c = 0; c < 3; ++c) {
-      const double ga = C.ga[c][j];
-      const double gv_h = __dmul_rn(hh, C.gv[c][j]);
-      lam[c] = all ? ga : __dadd_rn(ga, gv_h);
-      Sl.lam[c][k] = lam[c];
-      Sl.gp0[c][k] = all ? 0.0 : C.gr[c][j];
-      C.ga[c][j] = all ? 0.0 : gv_h;
-      if (!all) C.gr[c][j] = 0.0;
-      Sl.ap[c][k] = p[c];
+    // end of the step at F.T
+    if (F.active) {
+      double gp[3];
+      for (int c = 0; c < 3; ++c) {
+        gp[c] = mj * G[c];
+        if (kf >= 0) gp[c] = gp0[c] + (gp[c] - u[c]);
+      }
+      if (!isfinite(gp[0]) || !isfinite(gp[1]) || !isfinite(gp[2]) ||
+          !isfinite(G[3]))
+        atomicOr(err, 1);
+      gm += G[3];
+      const double h = tick_h(F.T, tau0, inv_ticks);
+      const double hh2 = 0.5 * h * h;
+      for (int c = 0; c < 3; ++c) {
+        gr[c] += gp[c];
+        gv[c] += h * gp[c];
+        ga[c] += hh2 * gp[c];
+      }
+      C.gm[j] = gm;
     }
-    if (mixed) {
-      float4 hi, lo;
-      pack_ds(p[0], p[1], p[2], 0.f, hi, lo);
-      Sl.ahi[k] = hi;
-      Sl.alo[k] = lo;
-      Sl.alam[k] = make_float4((float)lam[0], (float)lam[1], (float)lam[2], 0.f);
+    // start of the step at R.T
+    if (R.active) {
+      const AdjSlots& Sl = R.Sl;
+      const double h = tick_h(R.T, tau1, inv_ticks);
+      double p[3];
+      for (int c = 0; c < 3; ++c) {
+        double vp;
+        taylor1(r[c], v[c], a[c], h, p[c], vp);
+      }
+      if (kr >= 0 && !R.all) {
+        for (int c = 0; c < 3; ++c) {
+          St.r[c][j] = r[c];
+          St.v[c][j] = v[c];
+          St.a[c][j] = a[c];
+        }
+        St.tau[j] = tau1;
+        cur_e[j] = pe;
+      }
+      Sl.slot[j] = kr;
+      store_pred(j, p, mf, mixed, P);
+      if (kr >= 0) {
+        const double hh = __dmul_rn(0.5, h);
+        double lam[3];
+        for (int c = 0; c < 3; ++c) {
+          const double gv_h = __dmul_rn(hh, gv[c]);
+          lam[c] = R.all ? ga[c] : __dadd_rn(ga[c], gv_h);
+          Sl.lam[c][kr] = lam[c];
+          Sl.gp0[c][kr] = R.all ? 0.0 : gr[c];
+          Sl.ap[c][kr] = p[c];
+          ga[c] = R.all ? 0.0 : gv_h;
+          if (!R.all) gr[c] = 0.0;
+        }
+        if (mixed) {
+          float4 hi, lo;
+          pack_ds(p[0], p[1], p[2], 0.f, hi, lo);
+          Sl.ahi[kr] = hi;
+          Sl.alo[kr] = lo;
+          Sl.alam[kr] =
+              make_float4((float)lam[0], (float)lam[1], (float)lam[2], 0.f);
+        }
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      C.gr[c][j] = gr[c];
+      C.gv[c][j] = gv[c];
+      C.ga[c][j] = ga[c];
     }
   }
 }
 
+// ---------------------------------------------------------------------
+// Force vector-Jacobian product
+// ---------------------------------------------------------------------
+//
+// i side: for active slot k (body i), u_k = sum_{j != i} g_ij
+//   = lam_i W_i - 3 U_i,  W_i = sum m_j / s^3,
+//   U_i = sum m_j (lam_i . d_ij) d_ij / s^5.
+// j side: for body j, G_j = sum_{i in A, i != j} (lam_i / s^3
+//   - 3 (lam_i . d_ij) d_ij / s^5) and Z_j = sum lam_i . d_ij / s^3, with
+// d_ij = p_j - p_i; body j's position cotangent gets m_j G_j, its mass
+// cotangent Z_j.
+//
+// Work split (both sides): a block holds IG = 128 / tpt targets with tpt
+// lanes each and runs one of S chunks of the sources. Lane sums are added
+// in a fixed shuffle tree; with S > 1 each block writes one partial per
+// target and the last block of the group to finish (counted with an
+// atomic) adds the S partials in split order, so the result does not
+// depend on which block finished first.
+
 struct VjpArgs {
   int n, n_act;
-  const int* idx;
-  const int* slot;
+  const int* idx;   // body of each active slot
   double eps2;
   float eps2f;
   AdjPred P;
   AdjSlots Sl;
   VjpShape V;
   int iblocks;
-  double* part_i;  // [S_i][3][n_act]
-  double* part_j;  // [S_j][4][n]
+  VjpOut O;
+};
+
+struct VjpSm {
+  int last;
+  double sums[4][kAdjThreads];
 };
 
 template <int kN>
@@ -249,206 +463,513 @@ __device__ __forceinline__ void lane_reduce(double (&x)[kN], int tpt) {
     for (int c = 0; c < kN; ++c) x[c] += __shfl_xor_sync(kFull, x[c], o);
 }
 
-// i side: for active slot k (body i), u_k = sum_{j != i} g_ij
-//   = lam_i W_i - 3 U_i,  W_i = sum m_j / s^3,
-//   U_i = sum m_j (lam_i . d_ij) d_ij / s^5.
-template <int kMixed>
-__device__ __forceinline__ void vjp_i_side(const VjpArgs& A, int b) {
-  const VjpSide& V = A.V.si;
-  const int tpb = kAdjThreads / V.tpt;
-  const int g = b / V.S, sp = b - g * V.S;
-  const int k = g * tpb + threadIdx.x / V.tpt;
-  const int lane = threadIdx.x & (V.tpt - 1);
-  const bool live = k < A.n_act;
-  const int beg = sp * V.chunk;
-  const int end = live ? min(A.n, beg + V.chunk) : beg;
-  const int bi = live ? A.idx[k] : -1;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // W, U
-  if (kMixed) {
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 ih = live ? A.Sl.ahi[k] : z4;
-    const float4 il = live ? A.Sl.alo[k] : z4;
-    const float4 lm = live ? A.Sl.alam[k] : z4;
-    for (int j0 = beg + lane; j0 < end; j0 += V.tpt * kFold) {
-      const int j1 = min(end, j0 + V.tpt * kFold);
-      float w = 0.f, u0 = 0.f, u1 = 0.f, u2 = 0.f;
-      for (int j = j0; j < j1; j += V.tpt) {
-        const float4 jh = A.P.jhi[j], jl = A.P.jlo[j];
-        const float dx = (jh.x - ih.x) + (jl.x - il.x);
-        const float dy = (jh.y - ih.y) + (jl.y - il.y);
-        const float dz = (jh.z - ih.z) + (jl.z - il.z);
-        const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, A.eps2f)));
-        const float rs = (j == bi) ? 0.f : rsqrtf(s2);
-        const float rs2 = rs * rs;
-        const float mr3 = jh.w * rs2 * rs;
-        const float ld = fmaf(lm.x, dx, fmaf(lm.y, dy, lm.z * dz));
-        const float cc = mr3 * rs2 * ld;
-        w += mr3;
-        u0 = fmaf(cc, dx, u0);
-        u1 = fmaf(cc, dy, u1);
-        u2 = fmaf(cc, dz, u2);
-      }
-      acc[0] += w;
-      acc[1] += u0;
-      acc[2] += u1;
-      acc[3] += u2;
-    }
-  } else {
-    double ix = 0, iy = 0, iz = 0, lx = 0, ly = 0, lz = 0;
-    if (live) {
-      ix = A.Sl.ap[0][k];
-      iy = A.Sl.ap[1][k];
-      iz = A.Sl.ap[2][k];
-      lx = A.Sl.lam[0][k];
-      ly = A.Sl.lam[1][k];
-      lz = A.Sl.lam[2][k];
-    }
-    for (int j = beg + lane; j < end; j += V.tpt) {
-      const double dx = A.P.p[0][j] - ix;
-      const double dy = A.P.p[1][j] - iy;
-      const double dz = A.P.p[2][j] - iz;
-      const double s2 = dx * dx + dy * dy + dz * dz + A.eps2;
-      const double rs = (j == bi) ? 0.0 : rsqrt(s2);
-      const double rs2 = rs * rs;
-      const double mr3 = A.P.m[j] * rs2 * rs;
-      const double cc = mr3 * rs2 * (lx * dx + ly * dy + lz * dz);
-      acc[0] += mr3;
-      acc[1] += cc * dx;
-      acc[2] += cc * dy;
-      acc[3] += cc * dz;
-    }
-  }
-  lane_reduce(acc, V.tpt);
-  if (live && lane == 0) {
+struct VjpBlock {
+  int g;        // target group
+  int sp;       // source split
+  int t0;       // first target of the group
+  int tl;       // this thread's target within the group
+  int tgt;      // its target
+  int lane;     // its lane among the target's tpt threads
+  int beg, end; // source range of the split
+  bool live;
+};
+
+__device__ __forceinline__ VjpBlock vjp_block(const VjpSide& V, int b,
+                                              int n_targets, int n_sources) {
+  VjpBlock B;
+  const int ig = kAdjThreads / V.tpt;
+  B.g = b / V.S;
+  B.sp = b - B.g * V.S;
+  B.t0 = B.g * ig;
+  B.tl = threadIdx.x / V.tpt;
+  B.tgt = B.t0 + B.tl;
+  B.lane = threadIdx.x & (V.tpt - 1);
+  B.live = B.tgt < n_targets;
+  B.beg = B.sp * V.chunk;
+  B.end = min(n_sources, B.beg + V.chunk);
+  return B;
+}
+
+// the reduced sums of one target: i side (kSide 0) u = lam W - 3 U into
+// O.u; j side (kSide 1) G, Z into O.g; replay force (kSide 2) into O.f
+template <int kSide>
+__device__ __forceinline__ void vjp_store(const VjpArgs& A, int t,
+                                          const double (&x)[4]) {
+  if (kSide == 0) {
     for (int c = 0; c < 3; ++c)
-      A.part_i[((long long)sp * 3 + c) * A.n_act + k] =
-          A.Sl.lam[c][k] * acc[0] - 3.0 * acc[1 + c];
-  }
-}
-
-// j side: for body j, G_j = sum_{i in A, i != j} (lam_i / s^3
-//   - 3 (lam_i . d_ij) d_ij / s^5) and Z_j = sum lam_i . d_ij / s^3, with
-// d_ij = p_j - p_i; body j's position cotangent gets m_j G_j, its mass
-// cotangent Z_j.
-template <int kMixed>
-__device__ __forceinline__ void vjp_j_side(const VjpArgs& A, int b) {
-  const VjpSide& V = A.V.sj;
-  const int tpb = kAdjThreads / V.tpt;
-  const int g = b / V.S, sp = b - g * V.S;
-  const int j = g * tpb + threadIdx.x / V.tpt;
-  const int lane = threadIdx.x & (V.tpt - 1);
-  const bool live = j < A.n;
-  const int beg = sp * V.chunk;
-  const int end = live ? min(A.n_act, beg + V.chunk) : beg;
-  const int sj = live ? A.slot[j] : -1;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // G, Z
-  if (kMixed) {
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 jh = live ? A.P.jhi[j] : z4;
-    const float4 jl = live ? A.P.jlo[j] : z4;
-    for (int k0 = beg + lane; k0 < end; k0 += V.tpt * kFold) {
-      const int k1 = min(end, k0 + V.tpt * kFold);
-      float g0 = 0.f, g1 = 0.f, g2 = 0.f, zz = 0.f;
-      for (int k = k0; k < k1; k += V.tpt) {
-        const float4 ah = A.Sl.ahi[k], al = A.Sl.alo[k], lm = A.Sl.alam[k];
-        const float dx = (jh.x - ah.x) + (jl.x - al.x);
-        const float dy = (jh.y - ah.y) + (jl.y - al.y);
-        const float dz = (jh.z - ah.z) + (jl.z - al.z);
-        const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, A.eps2f)));
-        const float rs = (k == sj) ? 0.f : rsqrtf(s2);
-        const float rs2 = rs * rs;
-        const float rs3 = rs2 * rs;
-        const float t = fmaf(lm.x, dx, fmaf(lm.y, dy, lm.z * dz)) * rs3;
-        const float cc = -3.f * t * rs2;
-        zz += t;
-        g0 = fmaf(cc, dx, fmaf(rs3, lm.x, g0));
-        g1 = fmaf(cc, dy, fmaf(rs3, lm.y, g1));
-        g2 = fmaf(cc, dz, fmaf(rs3, lm.z, g2));
-      }
-      acc[0] += g0;
-      acc[1] += g1;
-      acc[2] += g2;
-      acc[3] += zz;
-    }
+      A.O.u[c][t] = A.Sl.lam[c][t] * x[0] - 3.0 * x[1 + c];
+  } else if (kSide == 1) {
+    for (int c = 0; c < 4; ++c) A.O.g[c][t] = x[c];
   } else {
-    double px = 0, py = 0, pz = 0;
-    if (live) {
-      px = A.P.p[0][j];
-      py = A.P.p[1][j];
-      pz = A.P.p[2][j];
-    }
-    for (int k = beg + lane; k < end; k += V.tpt) {
-      const double lx = A.Sl.lam[0][k], ly = A.Sl.lam[1][k],
-                   lz = A.Sl.lam[2][k];
-      const double dx = px - A.Sl.ap[0][k];
-      const double dy = py - A.Sl.ap[1][k];
-      const double dz = pz - A.Sl.ap[2][k];
-      const double s2 = dx * dx + dy * dy + dz * dz + A.eps2;
-      const double rs = (k == sj) ? 0.0 : rsqrt(s2);
-      const double rs2 = rs * rs;
-      const double rs3 = rs2 * rs;
-      const double t = (lx * dx + ly * dy + lz * dz) * rs3;
-      const double cc = -3.0 * t * rs2;
-      acc[0] += rs3 * lx + cc * dx;
-      acc[1] += rs3 * ly + cc * dy;
-      acc[2] += rs3 * lz + cc * dz;
-      acc[3] += t;
-    }
+    for (int c = 0; c < 3; ++c) A.O.f[c][t] = x[c];
   }
+}
+
+template <int kSide>
+__device__ __forceinline__ void vjp_finish(const VjpArgs& A, const VjpSide& V,
+                                           const VjpBlock& B, int n_targets,
+                                           double (&acc)[4], double* part,
+                                           int* cnt, VjpSm& sm) {
   lane_reduce(acc, V.tpt);
-  if (live && lane == 0) {
-    for (int c = 0; c < 4; ++c)
-      A.part_j[((long long)sp * 4 + c) * A.n + j] = acc[c];
+  if (V.S == 1) {
+    if (B.live && B.lane == 0) vjp_store<kSide>(A, B.tgt, acc);
+    return;
   }
+  const int ig = kAdjThreads / V.tpt;
+  double* gp = part + (long long)B.g * V.S * 4 * ig;
+  if (B.lane == 0)
+    for (int c = 0; c < 4; ++c) gp[((long long)B.sp * 4 + c) * ig + B.tl] = acc[c];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sm.last = atomicAdd(&cnt[B.g], 1) == V.S - 1;
+  __syncthreads();
+  if (!sm.last) return;
+  __threadfence();
+  for (int o = threadIdx.x; o < 4 * ig; o += kAdjThreads) {
+    const int c = o / ig, t = o - c * ig;
+    const double* q = gp + (long long)c * ig + t;
+    const long long stride = 4LL * ig;
+    double x = 0.0;
+    int sp = 0;
+    // eight loads in flight, then added in split order
+    for (; sp + 8 <= V.S; sp += 8) {
+      double y[8];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) y[w] = __ldcg(q + (sp + w) * stride);
+#pragma unroll
+      for (int w = 0; w < 8; ++w) x += y[w];
+    }
+    for (; sp < V.S; ++sp) x += __ldcg(q + sp * stride);
+    sm.sums[c][t] = x;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ig; t += kAdjThreads) {
+    if (B.t0 + t < n_targets) {
+      const double x[4] = {sm.sums[0][t], sm.sums[1][t], sm.sums[2][t],
+                           sm.sums[3][t]};
+      vjp_store<kSide>(A, B.t0 + t, x);
+    }
+  }
+  if (threadIdx.x == 0) cnt[B.g] = 0;  // ready for the next launch
+}
+
+// FP64: plain loops over the sources, FP64 sums.
+__device__ __forceinline__ void vjp_i_f64(const VjpArgs& A, int b, VjpSm& sm) {
+  const VjpSide& V = A.V.si;
+  const VjpBlock B = vjp_block(V, b, A.n_act, A.n);
+  const int k = B.tgt;
+  const int end = B.live ? B.end : B.beg;
+  const int bi = B.live ? A.idx[k] : -1;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // W, U
+  double ix = 0, iy = 0, iz = 0, lx = 0, ly = 0, lz = 0;
+  if (B.live) {
+    ix = A.Sl.ap[0][k];
+    iy = A.Sl.ap[1][k];
+    iz = A.Sl.ap[2][k];
+    lx = A.Sl.lam[0][k];
+    ly = A.Sl.lam[1][k];
+    lz = A.Sl.lam[2][k];
+  }
+  for (int j = B.beg + B.lane; j < end; j += V.tpt) {
+    const double dx = A.P.p[0][j] - ix;
+    const double dy = A.P.p[1][j] - iy;
+    const double dz = A.P.p[2][j] - iz;
+    const double s2 = dx * dx + dy * dy + dz * dz + A.eps2;
+    const double rs = (j == bi) ? 0.0 : rsqrt(s2);
+    const double rs2 = rs * rs;
+    const double mr3 = A.P.m[j] * rs2 * rs;
+    const double cc = mr3 * rs2 * (lx * dx + ly * dy + lz * dz);
+    acc[0] += mr3;
+    acc[1] += cc * dx;
+    acc[2] += cc * dy;
+    acc[3] += cc * dz;
+  }
+  vjp_finish<0>(A, V, B, A.n_act, acc, A.O.part_i, A.O.cnt_i, sm);
+}
+
+__device__ __forceinline__ void vjp_j_f64(const VjpArgs& A, int b, VjpSm& sm) {
+  const VjpSide& V = A.V.sj;
+  const VjpBlock B = vjp_block(V, b, A.n, A.n_act);
+  const int j = B.tgt;
+  const int end = B.live ? B.end : B.beg;
+  const int sj = B.live ? A.Sl.slot[j] : -1;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // G, Z
+  double px = 0, py = 0, pz = 0;
+  if (B.live) {
+    px = A.P.p[0][j];
+    py = A.P.p[1][j];
+    pz = A.P.p[2][j];
+  }
+  for (int k = B.beg + B.lane; k < end; k += V.tpt) {
+    const double lx = A.Sl.lam[0][k], ly = A.Sl.lam[1][k],
+                 lz = A.Sl.lam[2][k];
+    const double dx = px - A.Sl.ap[0][k];
+    const double dy = py - A.Sl.ap[1][k];
+    const double dz = pz - A.Sl.ap[2][k];
+    const double s2 = dx * dx + dy * dy + dz * dz + A.eps2;
+    const double rs = (k == sj) ? 0.0 : rsqrt(s2);
+    const double rs2 = rs * rs;
+    const double rs3 = rs2 * rs;
+    const double t = (lx * dx + ly * dy + lz * dz) * rs3;
+    const double cc = -3.0 * t * rs2;
+    acc[0] += rs3 * lx + cc * dx;
+    acc[1] += rs3 * ly + cc * dy;
+    acc[2] += rs3 * lz + cc * dz;
+    acc[3] += t;
+  }
+  vjp_finish<1>(A, V, B, A.n, acc, A.O.part_j, A.O.cnt_j, sm);
+}
+
+// Mixed: sources staged in shared memory by tiles of kVjpTile, structure of
+// arrays, and taken four at a time (128-bit shared loads) as two packed
+// pairs; every FMA-pipe operation works on two sources at once (f32x2).
+// A tile is padded to a multiple of 4 tpt with neutral sources (zero mass
+// or zero lam, far away), so every lane runs the same packed loop. A warp
+// whose target sits in the tile runs the masked loop, where the target's
+// own pair gets 1/s = 0 and adds exact zeros.
+constexpr int kVjpTile = TSBTS_VJP_TILE;
+constexpr float kFar = 1.0e18f;
+
+struct __align__(16) VjpTileI {
+  float xh[kVjpTile], yh[kVjpTile], zh[kVjpTile], m[kVjpTile];
+  float xl[kVjpTile], yl[kVjpTile], zl[kVjpTile];
+};
+struct __align__(16) VjpTileJ {
+  float xh[kVjpTile], yh[kVjpTile], zh[kVjpTile];
+  float xl[kVjpTile], yl[kVjpTile], zl[kVjpTile];
+  float lx[kVjpTile], ly[kVjpTile], lz[kVjpTile];
+};
+union VjpSmem {
+  VjpTileI i;
+  VjpTileJ j;
+};
+
+__device__ __forceinline__ ulonglong2 ld4(const float* p) {
+  return *reinterpret_cast<const ulonglong2*>(p);
+}
+
+// two sources (tile slots c, c + 1) on one active body: ii holds the
+// target's hi (0..2), lo (3..5) and lam (6..8), each broadcast to a pair
+template <bool kMask>
+__device__ __forceinline__ void pair_vjp_i2(const f2 (&ii)[9], f2 xh, f2 yh,
+                                            f2 zh, f2 m, f2 xl, f2 yl, f2 zl,
+                                            int c, int self, f2 e2, f2& W,
+                                            f2& Ux, f2& Uy, f2& Uz) {
+  const f2 dx = add2(sub2(xh, ii[0]), sub2(xl, ii[3]));
+  const f2 dy = add2(sub2(yh, ii[1]), sub2(yl, ii[4]));
+  const f2 dz = add2(sub2(zh, ii[2]), sub2(zl, ii[5]));
+  const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+  float s0, s1;
+  upk(s2, s0, s1);
+  float r0 = rsqrtf(s0), r1 = rsqrtf(s1);
+  if (kMask) {
+    if (c == self) r0 = 0.f;
+    if (c + 1 == self) r1 = 0.f;
+  }
+  const f2 rs = pk(r0, r1);
+  const f2 rs2 = mul2(rs, rs);
+  const f2 mr3 = mul2(mul2(m, rs), rs2);
+  const f2 ld = fma2(ii[6], dx, fma2(ii[7], dy, mul2(ii[8], dz)));
+  const f2 cc = mul2(mul2(mr3, rs2), ld);
+  W = add2(W, mr3);
+  Ux = fma2(cc, dx, Ux);
+  Uy = fma2(cc, dy, Uy);
+  Uz = fma2(cc, dz, Uz);
+}
+
+// two active sources (tile slots c, c + 1) on one body: jj holds the
+// target's hi (0..2) and lo (3..5)
+template <bool kMask>
+__device__ __forceinline__ void pair_vjp_j2(const f2 (&jj)[6], f2 xh, f2 yh,
+                                            f2 zh, f2 xl, f2 yl, f2 zl, f2 lx,
+                                            f2 ly, f2 lz, int c, int self,
+                                            f2 e2, f2 m3, f2& G0, f2& G1,
+                                            f2& G2, f2& Z) {
+  const f2 dx = add2(sub2(jj[0], xh), sub2(jj[3], xl));
+  const f2 dy = add2(sub2(jj[1], yh), sub2(jj[4], yl));
+  const f2 dz = add2(sub2(jj[2], zh), sub2(jj[5], zl));
+  const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+  float s0, s1;
+  upk(s2, s0, s1);
+  float r0 = rsqrtf(s0), r1 = rsqrtf(s1);
+  if (kMask) {
+    if (c == self) r0 = 0.f;
+    if (c + 1 == self) r1 = 0.f;
+  }
+  const f2 rs = pk(r0, r1);
+  const f2 rs2 = mul2(rs, rs);
+  const f2 rs3 = mul2(rs2, rs);
+  const f2 t = mul2(fma2(lx, dx, fma2(ly, dy, mul2(lz, dz))), rs3);
+  Z = add2(Z, t);
+  const f2 cc = mul2(mul2(t, rs2), m3);
+  G0 = fma2(cc, dx, fma2(rs3, lx, G0));
+  G1 = fma2(cc, dy, fma2(rs3, ly, G1));
+  G2 = fma2(cc, dz, fma2(rs3, lz, G2));
+}
+
+__device__ __forceinline__ float hsum(f2 x) {
+  float a, b;
+  upk(x, a, b);
+  return a + b;
+}
+
+__device__ __forceinline__ void vjp_i_mixed(const VjpArgs& A, int b,
+                                            VjpSmem& T0, VjpSm& sm) {
+  const VjpSide& V = A.V.si;
+  const VjpBlock B = vjp_block(V, b, A.n_act, A.n);
+  const int k = B.tgt;
+  const int bi = B.live ? A.idx[k] : -1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 ih = B.live ? A.Sl.ahi[k] : z4;
+  const float4 il = B.live ? A.Sl.alo[k] : z4;
+  const float4 lm = B.live ? A.Sl.alam[k] : z4;
+  const f2 ii[9] = {pk(ih.x, ih.x), pk(ih.y, ih.y), pk(ih.z, ih.z),
+                    pk(il.x, il.x), pk(il.y, il.y), pk(il.z, il.z),
+                    pk(lm.x, lm.x), pk(lm.y, lm.y), pk(lm.z, lm.z)};
+  const f2 e2 = pk(A.eps2f, A.eps2f);
+  const int step = 4 * V.tpt;
+  DS dacc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // W, U
+  VjpTileI& T = T0.i;
+  for (int jt = B.beg; jt < B.end; jt += kVjpTile) {
+    const int cnt = min(kVjpTile, B.end - jt);
+    const int cntp = (cnt + step - 1) / step * step;
+    __syncthreads();
+    for (int c = threadIdx.x; c < cntp; c += kAdjThreads) {
+      if (c < cnt) {
+        const float4 h = A.P.jhi[jt + c], l = A.P.jlo[jt + c];
+        T.xh[c] = h.x; T.yh[c] = h.y; T.zh[c] = h.z; T.m[c] = h.w;
+        T.xl[c] = l.x; T.yl[c] = l.y; T.zl[c] = l.z;
+      } else {
+        T.xh[c] = kFar; T.yh[c] = kFar; T.zh[c] = kFar; T.m[c] = 0.f;
+        T.xl[c] = 0.f; T.yl[c] = 0.f; T.zl[c] = 0.f;
+      }
+    }
+    __syncthreads();
+    const bool self_here = B.live && bi >= jt && bi < jt + cnt;
+    const int sc = self_here ? bi - jt : -1;
+    f2 W = pk(0.f, 0.f), Ux = W, Uy = W, Uz = W;
+    if (__any_sync(kFull, self_here)) {
+      for (int c = 4 * B.lane; c < cntp; c += step) {
+        const ulonglong2 xh = ld4(&T.xh[c]), yh = ld4(&T.yh[c]),
+                         zh = ld4(&T.zh[c]), m = ld4(&T.m[c]),
+                         xl = ld4(&T.xl[c]), yl = ld4(&T.yl[c]),
+                         zl = ld4(&T.zl[c]);
+        pair_vjp_i2<true>(ii, xh.x, yh.x, zh.x, m.x, xl.x, yl.x, zl.x, c, sc,
+                          e2, W, Ux, Uy, Uz);
+        pair_vjp_i2<true>(ii, xh.y, yh.y, zh.y, m.y, xl.y, yl.y, zl.y, c + 2,
+                          sc, e2, W, Ux, Uy, Uz);
+      }
+    } else {
+#pragma unroll kVjpUnroll
+      for (int c = 4 * B.lane; c < cntp; c += step) {
+        const ulonglong2 xh = ld4(&T.xh[c]), yh = ld4(&T.yh[c]),
+                         zh = ld4(&T.zh[c]), m = ld4(&T.m[c]),
+                         xl = ld4(&T.xl[c]), yl = ld4(&T.yl[c]),
+                         zl = ld4(&T.zl[c]);
+        pair_vjp_i2<false>(ii, xh.x, yh.x, zh.x, m.x, xl.x, yl.x, zl.x, c,
+                           -1, e2, W, Ux, Uy, Uz);
+        pair_vjp_i2<false>(ii, xh.y, yh.y, zh.y, m.y, xl.y, yl.y, zl.y, c + 2,
+                           -1, e2, W, Ux, Uy, Uz);
+      }
+    }
+    ds_add(dacc[0], hsum(W));
+    ds_add(dacc[1], hsum(Ux));
+    ds_add(dacc[2], hsum(Uy));
+    ds_add(dacc[3], hsum(Uz));
+  }
+  double acc[4];
+  for (int c = 0; c < 4; ++c) acc[c] = (double)dacc[c].hi + (double)dacc[c].lo;
+  vjp_finish<0>(A, V, B, A.n_act, acc, A.O.part_i, A.O.cnt_i, sm);
+}
+
+__device__ __forceinline__ void vjp_j_mixed(const VjpArgs& A, int b,
+                                            VjpSmem& T0, VjpSm& sm) {
+  const VjpSide& V = A.V.sj;
+  const VjpBlock B = vjp_block(V, b, A.n, A.n_act);
+  const int j = B.tgt;
+  const int sj = B.live ? A.Sl.slot[j] : -1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 th = B.live ? A.P.jhi[j] : z4;
+  const float4 tl = B.live ? A.P.jlo[j] : z4;
+  const f2 jj[6] = {pk(th.x, th.x), pk(th.y, th.y), pk(th.z, th.z),
+                    pk(tl.x, tl.x), pk(tl.y, tl.y), pk(tl.z, tl.z)};
+  const f2 e2 = pk(A.eps2f, A.eps2f);
+  const f2 m3 = pk(-3.f, -3.f);
+  const int step = 4 * V.tpt;
+  DS dacc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // G, Z
+  VjpTileJ& T = T0.j;
+  for (int kt = B.beg; kt < B.end; kt += kVjpTile) {
+    const int cnt = min(kVjpTile, B.end - kt);
+    const int cntp = (cnt + step - 1) / step * step;
+    __syncthreads();
+    for (int c = threadIdx.x; c < cntp; c += kAdjThreads) {
+      if (c < cnt) {
+        const float4 h = A.Sl.ahi[kt + c], l = A.Sl.alo[kt + c],
+                     lm = A.Sl.alam[kt + c];
+        T.xh[c] = h.x; T.yh[c] = h.y; T.zh[c] = h.z;
+        T.xl[c] = l.x; T.yl[c] = l.y; T.zl[c] = l.z;
+        T.lx[c] = lm.x; T.ly[c] = lm.y; T.lz[c] = lm.z;
+      } else {
+        T.xh[c] = kFar; T.yh[c] = kFar; T.zh[c] = kFar;
+        T.xl[c] = 0.f; T.yl[c] = 0.f; T.zl[c] = 0.f;
+        T.lx[c] = 0.f; T.ly[c] = 0.f; T.lz[c] = 0.f;
+      }
+    }
+    __syncthreads();
+    const bool self_here = sj >= kt && sj < kt + cnt;
+    const int sc = self_here ? sj - kt : -1;
+    f2 G0 = pk(0.f, 0.f), G1 = G0, G2 = G0, Z = G0;
+    if (__any_sync(kFull, self_here)) {
+      for (int c = 4 * B.lane; c < cntp; c += step) {
+        const ulonglong2 xh = ld4(&T.xh[c]), yh = ld4(&T.yh[c]),
+                         zh = ld4(&T.zh[c]), xl = ld4(&T.xl[c]),
+                         yl = ld4(&T.yl[c]), zl = ld4(&T.zl[c]),
+                         lx = ld4(&T.lx[c]), ly = ld4(&T.ly[c]),
+                         lz = ld4(&T.lz[c]);
+        pair_vjp_j2<true>(jj, xh.x, yh.x, zh.x, xl.x, yl.x, zl.x, lx.x, ly.x,
+                          lz.x, c, sc, e2, m3, G0, G1, G2, Z);
+        pair_vjp_j2<true>(jj, xh.y, yh.y, zh.y, xl.y, yl.y, zl.y, lx.y, ly.y,
+                          lz.y, c + 2, sc, e2, m3, G0, G1, G2, Z);
+      }
+    } else {
+#pragma unroll kVjpUnroll
+      for (int c = 4 * B.lane; c < cntp; c += step) {
+        const ulonglong2 xh = ld4(&T.xh[c]), yh = ld4(&T.yh[c]),
+                         zh = ld4(&T.zh[c]), xl = ld4(&T.xl[c]),
+                         yl = ld4(&T.yl[c]), zl = ld4(&T.zl[c]),
+                         lx = ld4(&T.lx[c]), ly = ld4(&T.ly[c]),
+                         lz = ld4(&T.lz[c]);
+        pair_vjp_j2<false>(jj, xh.x, yh.x, zh.x, xl.x, yl.x, zl.x, lx.x,
+                           ly.x, lz.x, c, -1, e2, m3, G0, G1, G2, Z);
+        pair_vjp_j2<false>(jj, xh.y, yh.y, zh.y, xl.y, yl.y, zl.y, lx.y,
+                           ly.y, lz.y, c + 2, -1, e2, m3, G0, G1, G2, Z);
+      }
+    }
+    ds_add(dacc[0], hsum(G0));
+    ds_add(dacc[1], hsum(G1));
+    ds_add(dacc[2], hsum(G2));
+    ds_add(dacc[3], hsum(Z));
+  }
+  double acc[4];
+  for (int c = 0; c < 4; ++c) acc[c] = (double)dacc[c].hi + (double)dacc[c].lo;
+  vjp_finish<1>(A, V, B, A.n, acc, A.O.part_j, A.O.cnt_j, sm);
+}
+
+// Replay force (mixed): a_i = sum_{j != i} m_j d_ij / s^3 for the active
+// bodies at the predicted positions, with the i side's work split, tiles
+// and packed pair loop; the sums are double-single per lane, FP64 after.
+template <bool kMask>
+__device__ __forceinline__ void pair_force2(const f2 (&ii)[6], f2 xh, f2 yh,
+                                            f2 zh, f2 m, f2 xl, f2 yl, f2 zl,
+                                            int c, int self, f2 e2, f2& ax,
+                                            f2& ay, f2& az) {
+  const f2 dx = add2(sub2(xh, ii[0]), sub2(xl, ii[3]));
+  const f2 dy = add2(sub2(yh, ii[1]), sub2(yl, ii[4]));
+  const f2 dz = add2(sub2(zh, ii[2]), sub2(zl, ii[5]));
+  const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+  float s0, s1;
+  upk(s2, s0, s1);
+  float r0 = rsqrtf(s0), r1 = rsqrtf(s1);
+  if (kMask) {
+    if (c == self) r0 = 0.f;
+    if (c + 1 == self) r1 = 0.f;
+  }
+  const f2 rs = pk(r0, r1);
+  const f2 mr3 = mul2(mul2(m, rs), mul2(rs, rs));
+  ax = fma2(mr3, dx, ax);
+  ay = fma2(mr3, dy, ay);
+  az = fma2(mr3, dz, az);
+}
+
+__device__ __forceinline__ void force_mixed(const VjpArgs& A, int b,
+                                            VjpSmem& T0, VjpSm& sm) {
+  const VjpSide& V = A.V.si;
+  const VjpBlock B = vjp_block(V, b, A.n_act, A.n);
+  const int bi = B.live ? A.idx[B.tgt] : -1;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 ih = B.live ? A.P.jhi[bi] : z4;
+  const float4 il = B.live ? A.P.jlo[bi] : z4;
+  const f2 ii[6] = {pk(ih.x, ih.x), pk(ih.y, ih.y), pk(ih.z, ih.z),
+                    pk(il.x, il.x), pk(il.y, il.y), pk(il.z, il.z)};
+  const f2 e2 = pk(A.eps2f, A.eps2f);
+  const int step = 4 * V.tpt;
+  DS dacc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  VjpTileI& T = T0.i;
+  for (int jt = B.beg; jt < B.end; jt += kVjpTile) {
+    const int cnt = min(kVjpTile, B.end - jt);
+    const int cntp = (cnt + step - 1) / step * step;
+    __syncthreads();
+    for (int c = threadIdx.x; c < cntp; c += kAdjThreads) {
+      if (c < cnt) {
+        const float4 h = A.P.jhi[jt + c], l = A.P.jlo[jt + c];
+        T.xh[c] = h.x; T.yh[c] = h.y; T.zh[c] = h.z; T.m[c] = h.w;
+        T.xl[c] = l.x; T.yl[c] = l.y; T.zl[c] = l.z;
+      } else {
+        T.xh[c] = kFar; T.yh[c] = kFar; T.zh[c] = kFar; T.m[c] = 0.f;
+        T.xl[c] = 0.f; T.yl[c] = 0.f; T.zl[c] = 0.f;
+      }
+    }
+    __syncthreads();
+    const bool self_here = B.live && bi >= jt && bi < jt + cnt;
+    const int sc = self_here ? bi - jt : -1;
+    f2 ax = pk(0.f, 0.f), ay = ax, az = ax;
+    if (__any_sync(kFull, self_here)) {
+      for (int c = 4 * B.lane; c < cntp; c += step) {
+        const ulonglong2 xh = ld4(&T.xh[c]), yh = ld4(&T.yh[c]),
+                         zh = ld4(&T.zh[c]), m = ld4(&T.m[c]),
+                         xl = ld4(&T.xl[c]), yl = ld4(&T.yl[c]),
+                         zl = ld4(&T.zl[c]);
+        pair_force2<true>(ii, xh.x, yh.x, zh.x, m.x, xl.x, yl.x, zl.x, c, sc,
+                          e2, ax, ay, az);
+        pair_force2<true>(ii, xh.y, yh.y, zh.y, m.y, xl.y, yl.y, zl.y, c + 2,
+                          sc, e2, ax, ay, az);
+      }
+    } else {
+#pragma unroll kVjpUnroll
+      for (int c = 4 * B.lane; c < cntp; c += step) {
+        const ulonglong2 xh = ld4(&T.xh[c]), yh = ld4(&T.yh[c]),
+                         zh = ld4(&T.zh[c]), m = ld4(&T.m[c]),
+                         xl = ld4(&T.xl[c]), yl = ld4(&T.yl[c]),
+                         zl = ld4(&T.zl[c]);
+        pair_force2<false>(ii, xh.x, yh.x, zh.x, m.x, xl.x, yl.x, zl.x, c, -1,
+                           e2, ax, ay, az);
+        pair_force2<false>(ii, xh.y, yh.y, zh.y, m.y, xl.y, yl.y, zl.y, c + 2,
+                           -1, e2, ax, ay, az);
+      }
+    }
+    ds_add(dacc[0], hsum(ax));
+    ds_add(dacc[1], hsum(ay));
+    ds_add(dacc[2], hsum(az));
+  }
+  double acc[4];
+  for (int c = 0; c < 3; ++c) acc[c] = (double)dacc[c].hi + (double)dacc[c].lo;
+  acc[3] = 0.0;
+  vjp_finish<2>(A, V, B, A.n_act, acc, A.O.part_i, A.O.cnt_i, sm);
+}
+
+__global__ void __launch_bounds__(kAdjThreads, kVjpMinBlocks)
+    adj_force_kernel(VjpArgs A) {
+  __shared__ VjpSm sm;
+  __shared__ VjpSmem tile;
+  force_mixed(A, blockIdx.x, tile, sm);
 }
 
 template <int kMixed>
-__global__ void __launch_bounds__(kAdjThreads) adj_vjp_kernel(VjpArgs A) {
+__global__ void __launch_bounds__(kAdjThreads, kVjpMinBlocks)
+    adj_vjp_kernel(VjpArgs A) {
   const int b = blockIdx.x;
-  if (b < A.iblocks)
-    vjp_i_side<kMixed>(A, b);
-  else
-    vjp_j_side<kMixed>(A, b - A.iblocks);
-}
-
-// Sum the splits, assemble the position cotangent of every body and pass
-// it through Eq. 2 to gr, gv, ga; add the mass cotangent.
-__global__ void adj_back_finalize_kernel(int n, int n_act, long long T,
-                                         double inv_ticks, int Si, int Sj,
-                                         const double* part_i,
-                                         const double* part_j, AdjPred P,
-                                         AdjSlots Sl, AdjState St, AdjCot C,
-                                         int* err) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += gridDim.x * blockDim.x) {
-    double G[4];
-    for (int c = 0; c < 4; ++c) G[c] = part_j[(long long)c * n + j];
-    for (int sp = 1; sp < Sj; ++sp)
-      for (int c = 0; c < 4; ++c)
-        G[c] += part_j[((long long)sp * 4 + c) * n + j];
-    const double m = P.m[j];
-    double gp[3];
-    for (int c = 0; c < 3; ++c) gp[c] = m * G[c];
-    const int k = Sl.slot[j];
-    if (k >= 0) {
-      for (int c = 0; c < 3; ++c) {
-        double u = part_i[(long long)c * n_act + k];
-        for (int sp = 1; sp < Si; ++sp)
-          u += part_i[((long long)sp * 3 + c) * n_act + k];
-        gp[c] = Sl.gp0[c][k] + (gp[c] - u);
-      }
-    }
-    if (!isfinite(gp[0]) || !isfinite(gp[1]) || !isfinite(gp[2]) ||
-        !isfinite(G[3]))
-      atomicOr(err, 1);
-    C.gm[j] += G[3];
-    const double h = tick_h(T, St.tau[j], inv_ticks);
-    const double hh2 = 0.5 * h * h;
-    for (int c = 0; c < 3; ++c) {
-      C.gr[c][j] += gp[c];
-      C.gv[c][j] += h * gp[c];
-      C.ga[c][j] += hh2 * gp[c];
-    }
+  __shared__ VjpSm sm;
+  if (kMixed) {
+    __shared__ VjpSmem tile;
+    if (b < A.iblocks)
+      vjp_i_mixed(A, b, tile, sm);
+    else
+      vjp_j_mixed(A, b - A.iblocks, tile, sm);
+  } else {
+    if (b < A.iblocks)
+      vjp_i_f64(A, b, sm);
+    else
+      vjp_j_f64(A, b - A.iblocks, sm);
   }
 }
 
@@ -525,28 +1046,37 @@ __global__ void soa_to_aos_kernel(int n, const double* x, const double* y,
 
 int grid_for(int n) { return std::max(1, std::min((n + 255) / 256, 4096)); }
 
+// per-body kernels of the step loop are latency-bound: small blocks spread
+// them over every SM
+constexpr int kBodyThreads = 64;
+int body_grid(int n) {
+  return std::max(1, std::min((n + kBodyThreads - 1) / kBodyThreads, 16384));
+}
+
+// Both sides: kVjpTpt lanes per target (more, up to 32, when the targets
+// are few; fewer when the sources are few), 128 / tpt targets per block
+// sharing each source tile, and as many source
+// splits (at most kVjpSmax, each lane at least 16 sources) as fill about
+// kVjpWant threads per SM.
 VjpSide choose_side(long long nt, long long ns, int sms) {
-  const long long want = (long long)sms * 1024;  // threads in flight
-  const long long min_chunk = 64;
+  const long long want = (long long)sms * kVjpWant;
+  int tpt = kVjpTpt;
+  // few targets: more lanes each, so that the block's threads are used
+  while (tpt < 32 && (kAdjThreads / (2 * tpt)) >= nt) tpt *= 2;
+  while (tpt > 1 && ns < 16LL * tpt) tpt >>= 1;
+  const int ig = kAdjThreads / tpt;
   VjpSide v{};
-  long long S = (want + nt - 1) / nt;
-  const long long smax = std::max<long long>(1, ns / min_chunk);
-  int tpt = 1;
-  if (S > smax) {
-    // too few sources to split further: several threads per target
-    const long long f = want / (nt * smax);
-    while (tpt < 32 && 2 * tpt <= f && ns / smax >= 32LL * tpt) tpt *= 2;
-    S = smax;
-  }
-  S = std::max<long long>(1, std::min<long long>(S, 1024));
-  long long chunk = (ns + S - 1) / S;
-  if (chunk < 1) chunk = 1;
-  S = (ns + chunk - 1) / chunk;
+  const long long groups = std::max<long long>(1, (nt + ig - 1) / ig);
+  long long S = (want + groups * kAdjThreads - 1) / (groups * kAdjThreads);
+  S = std::min<long long>(S, kVjpSmax);
+  S = std::min<long long>(S, std::max<long long>(1, ns / (16LL * tpt)));
+  S = std::max<long long>(S, 1);
+  long long chunk = std::max<long long>(1, (ns + S - 1) / S);
+  S = std::max<long long>(1, (ns + chunk - 1) / chunk);
   v.tpt = tpt;
-  v.S = (int)std::max<long long>(1, S);
+  v.S = (int)S;
   v.chunk = (int)chunk;
-  const int tpb = kAdjThreads / tpt;
-  v.groups = (int)((nt + tpb - 1) / tpb);
+  v.groups = (int)groups;
   return v;
 }
 
@@ -568,68 +1098,78 @@ void launch_adj_load(int n, const double* m_in, const double* r_in,
 }
 
 void launch_adj_init_accel(int n, const double* part, const int* nsplit,
-                           const AdjState& St, int* err, cudaStream_t s) {
-  adj_init_accel_kernel<<<grid_for(n), 256, 0, s>>>(n, part, nsplit, St, err);
+                           double* const fsum[3], long long T_next,
+                           double inv_ticks, int mixed, const AdjState& St,
+                           const AdjPred& P, int* err, cudaStream_t s) {
+  const FSum F{{fsum[0], fsum[1], fsum[2]}};
+  adj_init_accel_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(
+      n, part, nsplit, F, T_next, inv_ticks, mixed, St, P, err);
 }
 
 void launch_adj_predict(int n, long long T, double inv_ticks, int mixed,
                         const AdjState& St, const AdjPred& P, cudaStream_t s) {
-  adj_predict_kernel<<<grid_for(n), 256, 0, s>>>(n, T, inv_ticks, mixed, St,
-                                                 P);
+  adj_predict_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(n, T, inv_ticks,
+                                                           mixed, St, P);
 }
 
-void launch_adj_correct(int n_act, const int* idx, long long T,
-                        double inv_ticks, const double* part,
-                        const int* nsplit, const AdjState& St,
-                        const AdjPred& P, const AdjTape& Tp, long long e0,
-                        int* err, cudaStream_t s) {
-  // 32-thread blocks spread the FP64 work of small active sets over SMs
-  const int grid = std::max(1, std::min((n_act + 31) / 32, 8192));
-  adj_correct_kernel<<<grid, 32, 0, s>>>(n_act, idx, T, inv_ticks, part,
-                                         nsplit, St, P, Tp, e0, err);
+void launch_adj_correct_predict(int n, int n_act, long long T, long long e_lo,
+                                long long e_hi, long long T_next,
+                                double inv_ticks, int mixed,
+                                const double* part, const int* nsplit,
+                                double* const fsum[3], const AdjState& St,
+                                const AdjPred& P, const AdjTape& Tp,
+                                long long* fwd_e, const long long* next_e,
+                                int* err, cudaStream_t s) {
+  const FSum F{{fsum[0], fsum[1], fsum[2]}};
+  adj_correct_predict_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(
+      n, n_act, T, e_lo, e_hi, T_next, inv_ticks, mixed, part, nsplit, F, St,
+      P, Tp, fwd_e, next_e, err);
 }
 
-void launch_adj_back_prep(int n, long long T, double inv_ticks, long long e_lo,
-                          int all, int mixed, const AdjState& St,
-                          const AdjTape& Tp, long long* cur_e,
-                          const long long* prev_e, const AdjCot& C,
-                          const AdjPred& P, const AdjSlots& Sl,
-                          cudaStream_t s) {
-  adj_back_prep_kernel<<<grid_for(n), 256, 0, s>>>(
-      n, T, inv_ticks, e_lo, all, mixed, St, Tp, cur_e, prev_e, C, P, Sl);
+void launch_adj_force(int n, int n_act, const int* idx, double eps2,
+                      const AdjPred& P, const VjpSide& si, const VjpOut& O,
+                      cudaStream_t s) {
+  VjpArgs A{};
+  A.n = n;
+  A.n_act = n_act;
+  A.idx = idx;
+  A.eps2 = eps2;
+  A.eps2f = (float)eps2;
+  A.P = P;
+  A.V.si = si;
+  A.O = O;
+  adj_force_kernel<<<si.groups * si.S, kAdjThreads, 0, s>>>(A);
+}
+
+void launch_adj_back_step(int n, double inv_ticks, int mixed,
+                          const AdjBackFin& F, const AdjBackPrep& R,
+                          const AdjState& St, const AdjTape& Tp,
+                          long long* cur_e, const long long* prev_e,
+                          const AdjCot& C, const AdjPred& P, const VjpOut& O,
+                          int* err, cudaStream_t s) {
+  adj_back_step_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(
+      n, inv_ticks, mixed, F, R, St, Tp, cur_e, prev_e, C, P, O, err);
 }
 
 void launch_adj_vjp(int mixed, int n, int n_act, const int* idx, double eps2,
                     const AdjPred& P, const AdjSlots& Sl, const VjpShape& V,
-                    double* part_i, double* part_j, cudaStream_t s) {
+                    const VjpOut& O, cudaStream_t s) {
   VjpArgs A;
   A.n = n;
   A.n_act = n_act;
   A.idx = idx;
-  A.slot = Sl.slot;
   A.eps2 = eps2;
   A.eps2f = (float)eps2;
   A.P = P;
   A.Sl = Sl;
   A.V = V;
   A.iblocks = V.si.groups * V.si.S;
-  A.part_i = part_i;
-  A.part_j = part_j;
+  A.O = O;
   const int grid = A.iblocks + V.sj.groups * V.sj.S;
   if (mixed)
     adj_vjp_kernel<1><<<grid, kAdjThreads, 0, s>>>(A);
   else
     adj_vjp_kernel<0><<<grid, kAdjThreads, 0, s>>>(A);
-}
-
-void launch_adj_back_finalize(int n, int n_act, long long T, double inv_ticks,
-                              const VjpShape& V, const double* part_i,
-                              const double* part_j, const AdjPred& P,
-                              const AdjSlots& Sl, const AdjState& St,
-                              const AdjCot& C, int* err, cudaStream_t s) {
-  adj_back_finalize_kernel<<<grid_for(n), 256, 0, s>>>(
-      n, n_act, T, inv_ticks, V.si.S, V.sj.S, part_i, part_j, P, Sl, St, C,
-      err);
 }
 
 void launch_adj_loss(int n, const double* m, const AdjState& St, double* out,

@@ -99,8 +99,8 @@ struct AdjSlots {
   int* slot;
 };
 // work split of one side of the force vector-Jacobian product: `tpt`
-// threads per target (a power of two <= 32), S splits of `chunk` sources,
-// `groups` blocks of 128 / tpt targets per split
+// threads per target (a power of two <= 8), 128 / tpt targets per block,
+// S splits of `chunk` sources, `groups` target groups
 struct VjpSide {
   int tpt, S, chunk, groups;
 };
@@ -110,34 +110,72 @@ struct VjpShape {
   VjpSide si, sj;
 };
 VjpShape vjp_shape(int n, int n_act, int sms);
+// results of one force vector-Jacobian product: u[3] per active slot (i
+// side) and G[3], Z per body in g[4] (j side); split partials and the
+// per-group completion counters (zero between launches)
+struct VjpOut {
+  double* u[3];
+  double* g[4];
+  double* f[3];  // replay force sums per active slot
+  double* part_i;
+  double* part_j;
+  int* cnt_i;
+  int* cnt_j;
+};
+// the end of a reverse step (Eq. 2 adjoint of every body, with the force
+// cotangents of its VjpOut) and the start of the step before it (tape
+// restore, Eq. 1 adjoint, prediction); either may be inactive
+struct AdjBackFin {
+  int active;
+  long long T;
+  AdjSlots Sl;
+};
+struct AdjBackPrep {
+  int active;
+  int all;  // every body active at T = 0: the initial force
+  long long T;
+  long long e_lo;
+  AdjSlots Sl;
+};
 
 void launch_adj_load(int n, const double* m_in, const double* r_in,
                      const double* v_in, int mixed, double* m_out,
                      const AdjState& St, const AdjPred& P, int* err,
                      cudaStream_t s);
+// initial accelerations from the force partials, then the prediction to
+// T_next (< 0: none)
+// (fsum[0] != nullptr: the accelerations are fsum, else the force
+// kernel's split partials)
 void launch_adj_init_accel(int n, const double* part, const int* nsplit,
-                           const AdjState& St, int* err, cudaStream_t s);
+                           double* const fsum[3], long long T_next,
+                           double inv_ticks, int mixed, const AdjState& St,
+                           const AdjPred& P, int* err, cudaStream_t s);
 void launch_adj_predict(int n, long long T, double inv_ticks, int mixed,
                         const AdjState& St, const AdjPred& P, cudaStream_t s);
-void launch_adj_correct(int n_act, const int* idx, long long T,
-                        double inv_ticks, const double* part,
-                        const int* nsplit, const AdjState& St,
-                        const AdjPred& P, const AdjTape& Tp, long long e0,
-                        int* err, cudaStream_t s);
-void launch_adj_back_prep(int n, long long T, double inv_ticks, long long e_lo,
-                          int all, int mixed, const AdjState& St,
-                          const AdjTape& Tp, long long* cur_e,
-                          const long long* prev_e, const AdjCot& C,
-                          const AdjPred& P, const AdjSlots& Sl,
-                          cudaStream_t s);
+// Eq. 1 for the bodies of schedule entries [e_lo, e_hi) (fwd_e: each
+// body's next entry), then the prediction of every body to T_next
+void launch_adj_correct_predict(int n, int n_act, long long T, long long e_lo,
+                                long long e_hi, long long T_next,
+                                double inv_ticks, int mixed,
+                                const double* part, const int* nsplit,
+                                double* const fsum[3], const AdjState& St,
+                                const AdjPred& P, const AdjTape& Tp,
+                                long long* fwd_e, const long long* next_e,
+                                int* err, cudaStream_t s);
+// mixed replay force on the active bodies idx[0..n_act) into O.f (the i
+// side's work split)
+void launch_adj_force(int n, int n_act, const int* idx, double eps2,
+                      const AdjPred& P, const VjpSide& si, const VjpOut& O,
+                      cudaStream_t s);
+void launch_adj_back_step(int n, double inv_ticks, int mixed,
+                          const AdjBackFin& F, const AdjBackPrep& R,
+                          const AdjState& St, const AdjTape& Tp,
+                          long long* cur_e, const long long* prev_e,
+                          const AdjCot& C, const AdjPred& P, const VjpOut& O,
+                          int* err, cudaStream_t s);
 void launch_adj_vjp(int mixed, int n, int n_act, const int* idx, double eps2,
                     const AdjPred& P, const AdjSlots& Sl, const VjpShape& V,
-                    double* part_i, double* part_j, cudaStream_t s);
-void launch_adj_back_finalize(int n, int n_act, long long T, double inv_ticks,
-                              const VjpShape& V, const double* part_i,
-                              const double* part_j, const AdjPred& P,
-                              const AdjSlots& Sl, const AdjState& St,
-                              const AdjCot& C, int* err, cudaStream_t s);
+                    const VjpOut& O, cudaStream_t s);
 // L = sum m |r|^2 / sum m into out[0] (out[1] = sum m) and the cotangent
 // seeds dL/dr, dL/dm (velocity and acceleration cotangents zero)
 void launch_adj_loss(int n, const double* m, const AdjState& St, double* out,

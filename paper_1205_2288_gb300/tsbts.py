@@ -527,16 +527,20 @@ class Adjoint:
 
     schedule = (step_tau, step_off, act) as from final_pass_schedule.
     checkpoint_every = 0 tapes every step; K > 0 keeps a checkpoint every
-    K steps and recomputes during the reverse sweep."""
+    K steps and recomputes during the reverse sweep. graph_steps = 0 runs
+    plain stream launches; otherwise the forward replay and the reverse
+    sweep are each captured once as a CUDA graph and replayed."""
 
     def __init__(self, n, eps, schedule, *, precision=TSBTS_FP64, k_max=20,
-                 checkpoint_every=0, exact_order=-1, device=0, stream=None):
+                 checkpoint_every=0, exact_order=-1, device=0, stream=None,
+                 graph_steps=32):
         cfg = tsbts_config_default()
         cfg.precision = precision
         cfg.k_max = k_max
         cfg.exact_order = exact_order
         cfg.device = device
         cfg.stream = stream
+        cfg.graph_steps = graph_steps
         self.n = int(n)
         self.ctx = tsbts_create(cfg)
         try:

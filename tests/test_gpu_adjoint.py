@@ -95,6 +95,26 @@ def test_checkpointing_is_bit_identical(case600):
             np.testing.assert_array_equal(a, b)
 
 
+def test_graph_and_stream_launches_agree(case600):
+    c = case600
+    out = []
+    for K in (0, 16):
+        for graph_steps in (0, 32):
+            with tsbts.Adjoint(600, c["eps"], c["sched"], checkpoint_every=K,
+                               precision=tsbts.TSBTS_MIXED,
+                               graph_steps=graph_steps) as adj:
+                out.append(adj.loss_grad(c["m"], c["r"], c["v"]))
+                # a second call replays the captured graphs
+                again = adj.loss_grad(c["m"], c["r"], c["v"])
+                st = adj.stats()
+            for a, b in zip(again[1:], out[-1][1:]):
+                np.testing.assert_array_equal(a, b)
+            assert st["kernel_launches"] > 0
+    for o in out[1:]:
+        for a, b in zip(o[1:], out[0][1:]):
+            np.testing.assert_array_equal(a, b)
+
+
 def test_fp64_general_vjp_matches_oracle(case600):
     c = case600
     rng = np.random.default_rng(5)
