@@ -347,13 +347,24 @@ def adjoint_bench(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     m, r, v = inputs.plummer(n, SEED)
-    sim = tsbts.Simulation(m, r, v, eps=eps, eta=ETA, dt_max=DT_MAX,
-                           n_iter=N_ITER, era_mode=0, era_log2=2,
-                           precision=tsbts.TSBTS_MIXED)
-    sim.schedule_log(40_000_000)
-    sim.step_era(t_era)
-    sched = tsbts.final_pass_schedule(sim.schedule(), 0)
-    sim.close()
+    if args.schedule_in:
+        # a schedule saved by an earlier run (--schedule-out)
+        z = np.load(args.schedule_in)
+        sched = (z["tau"], z["off"], z["act"])
+    else:
+        sim = tsbts.Simulation(m, r, v, eps=eps, eta=ETA, dt_max=DT_MAX,
+                               n_iter=N_ITER, era_mode=0, era_log2=2,
+                               precision=tsbts.TSBTS_MIXED)
+        sim.schedule_log(40_000_000)
+        sim.step_era(t_era)
+        sched = tsbts.final_pass_schedule(sim.schedule(), 0)
+        sim.close()
+    if args.schedule_out:
+        np.savez(args.schedule_out, tau=sched[0], off=sched[1], act=sched[2])
+    if args.adjoint_steps:
+        # the first steps of the schedule only (a smaller case for profiling)
+        k = min(args.adjoint_steps, len(sched[0]))
+        sched = (sched[0][:k], sched[1][:k + 1], sched[2][:sched[1][k]])
     E = int(sched[1][-1])
     S = int(len(sched[0]))
     pairs = 3 * (E + n) * n
@@ -385,15 +396,22 @@ def adjoint_bench(args):
             ms = 0.0
             fwd = bwd = 0.0
             launches0 = adj.stats()["kernel_launches"]
-            for _ in range(reps):
+            for rep in range(reps):
                 flush.fill_(1)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
+                profiled = (args.profile_range and name == "mixed_taped"
+                            and rep == 0)
+                if profiled:
+                    torch.cuda.synchronize()
+                    torch.cuda.profiler.start()
                 e0.record(stream)
                 tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *g,
                                               device=True)
                 e1.record(stream)
                 e1.synchronize()
+                if profiled:
+                    torch.cuda.profiler.stop()
                 ms += e0.elapsed_time(e1)
                 st = adj.stats()
                 fwd += st["forward_ms"]
@@ -439,6 +457,7 @@ def adjoint_bench(args):
                    "n": n, "eps": eps, "eta": ETA, "dt_max": DT_MAX,
                    "era": "fixed 1/4", "n_iter": N_ITER,
                    "schedule_steps": S, "schedule_entries": E,
+                   "schedule_prefix_steps": args.adjoint_steps or None,
                    "loss": "sum m |r_T|^2 / sum m",
                    "l2": "256 MiB buffer written between timed gradients"},
         "pairs_per_gradient": pairs,
@@ -496,6 +515,17 @@ def main():
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--adjoint", action="store_true",
                     help="gradient through a frozen block schedule")
+    ap.add_argument("--schedule-out", default="",
+                    help="--adjoint: save the schedule (.npz)")
+    ap.add_argument("--schedule-in", default="",
+                    help="--adjoint: replay a saved schedule instead of "
+                         "integrating the era")
+    ap.add_argument("--adjoint-steps", type=int, default=0,
+                    help="--adjoint: use the schedule's first N steps")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="--adjoint: bracket the first timed mixed gradient "
+                         "with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     args = ap.parse_args()
     if args.force_sweep:
         return force_sweep(args)
