@@ -123,10 +123,76 @@ struct Corrected {
   int underflow;
 };
 
+// The body's next previous-pass records (time and step estimate), loaded
+// in one batch so that the cursor advance and the two Eq. 4 lookups of
+// Alg. 1 read registers instead of chaining dependent loads; records past
+// the window are read from memory.
+constexpr int kHistWin = 8;
+struct HistWin {
+  int base;
+  long long t[kHistWin];
+  double d[kHistWin];
+};
+
+__device__ __forceinline__ void load_hist_win(HistWin& W, const History& H,
+                                              int base, int end) {
+  W.base = base;
+#pragma unroll
+  for (int q = 0; q < kHistWin; ++q) {
+    const int c = base + q;
+    const bool in = c < end;
+    W.t[q] = in ? H.tau[c] : LLONG_MAX;
+    W.d[q] = in ? H.dts[c] : 0.0;
+  }
+}
+
+__device__ __forceinline__ long long win_tau(const HistWin& W,
+                                             const History& H, int c) {
+  const int q = c - W.base;
+  if (q < 0 || q >= kHistWin) return H.tau[c];
+  long long v = W.t[0];
+#pragma unroll
+  for (int k = 1; k < kHistWin; ++k)
+    if (q == k) v = W.t[k];
+  return v;
+}
+
+__device__ __forceinline__ double win_dts(const HistWin& W, const History& H,
+                                          int c) {
+  const int q = c - W.base;
+  if (q < 0 || q >= kHistWin) return H.dts[c];
+  double v = W.d[0];
+#pragma unroll
+  for (int k = 1; k < kHistWin; ++k)
+    if (q == k) v = W.d[k];
+  return v;
+}
+
+// history_dts_at on the window (same values, same arithmetic)
+__device__ __forceinline__ double history_dts_at_w(const HistWin& W,
+                                                   const History& H,
+                                                   int start, int end,
+                                                   long long t,
+                                                   double fallback) {
+  int c = start;
+  if (win_tau(W, H, c) > t) return fallback;
+  while (c + 1 < end && win_tau(W, H, c + 1) <= t) ++c;
+  const long long tc = win_tau(W, H, c);
+  if (tc == t) return win_dts(W, H, c);
+  if (c + 1 >= end) return fallback;
+  const long long tc1 = win_tau(W, H, c + 1);
+  const double dc = win_dts(W, H, c), dc1 = win_dts(W, H, c + 1);
+  const double w = __ddiv_rn((double)(t - tc), (double)(tc1 - tc));
+  return __dadd_rn(dc, __dmul_rn(__dsub_rn(dc1, dc), w));
+}
+
 // Active body i at block time tn with new acceleration an and criterion q:
 // Eq. 1 (position from Eq. 2, velocity kick), step estimate eta / sqrt(q),
 // the history record `rec`, and the next step (pass 0: standard block step;
 // passes >= 1: Alg. 1 with Eq. 4 against the previous pass's records).
+// Every load of the body comes before its stores (the arrays are reached
+// through pointers the compiler must assume may alias), so the body waits
+// for few dependent rounds of memory accesses.
 __device__ __forceinline__ Corrected correct_body(const Bodies& B,
                                                   const Params& P,
                                                   const History& cur,
@@ -134,27 +200,64 @@ __device__ __forceinline__ Corrected correct_body(const Bodies& B,
                                                   const double an[3], double q,
                                                   long long tn, int pass,
                                                   long long rec, int* err) {
+  // loads
+  const long long d = B.dt[i];
+  double r0[3], v0[3], a0[3];
+  for (int c = 0; c < 3; ++c) {
+    r0[c] = B.r[c][i];
+    v0[c] = B.v[c][i];
+    a0[c] = B.a[c][i];
+  }
+  const bool fits = rec < cur.cap;
+  const int sq = fits ? B.hcnt[i] : 0;
+  int start = 0, end = 0;
+  HistWin W;
+  if (pass != 0) {
+    start = B.cursor[i];
+    end = B.hoff[i + 1];
+    load_hist_win(W, prev, start, end);
+  }
   if (!isfinite(an[0]) || !isfinite(an[1]) || !isfinite(an[2]) ||
       !(q >= 0.0) || isnan(q))
     atomicOr(err, kErrNonFinite);
-  const long long d = B.dt[i];
+  // Eq. 1
   const double h = __dmul_rn((double)d, P.inv_ticks);
   double rn[3], vn[3];
   for (int c = 0; c < 3; ++c) {
     double rp, vp;
-    taylor1(B.r[c][i], B.v[c][i], B.a[c][i], h, rp, vp);
+    taylor1(r0[c], v0[c], a0[c], h, rp, vp);
     rn[c] = rp;
-    vn[c] = __dadd_rn(B.v[c][i],
-                      __dmul_rn(__dmul_rn(0.5, __dadd_rn(B.a[c][i], an[c])),
-                                h));
+    vn[c] = __dadd_rn(v0[c],
+                      __dmul_rn(__dmul_rn(0.5, __dadd_rn(a0[c], an[c])), h));
+  }
+  const double dts = __ddiv_rn(P.eta, __dsqrt_rn(q));
+  Corrected out;
+  out.d_old = d;
+  out.underflow = 0;
+  int new_cursor = -1;
+  if (pass == 0) {
+    out.d_new = forward_step(tn, d, dts, P.k_min, P.k_max, &out.underflow);
+  } else {
+    // advance the body's previous-pass cursor to the block time; the
+    // lookups below then read the few records that follow it
+    if (win_tau(W, prev, start) <= tn) {
+      while (start + 1 < end && win_tau(W, prev, start + 1) <= tn) ++start;
+      new_cursor = start;
+    }
+    const double e2 = history_dts_at_w(W, prev, start, end, tn + 2 * d, dts);
+    const double e1 = history_dts_at_w(W, prev, start, end, tn + d, dts);
+    out.d_new = symmetric_step(tn, d, dts, e2, e1, P.k_min, P.k_max,
+                               P.dtmax_t, &out.underflow);
+  }
+  // stores
+  for (int c = 0; c < 3; ++c) {
     B.r[c][i] = rn[c];
     B.v[c][i] = vn[c];
     B.a[c][i] = an[c];
   }
   B.tau[i] = tn;
-  const double dts = __ddiv_rn(P.eta, __dsqrt_rn(q));
   B.dts[i] = dts;
-  if (rec < cur.cap) {
+  if (fits) {
     cur.tau[rec] = tn;
     for (int c = 0; c < 3; ++c) {
       cur.r[c][rec] = rn[c];
@@ -163,31 +266,12 @@ __device__ __forceinline__ Corrected correct_body(const Bodies& B,
     }
     cur.dts[rec] = dts;
     cur.body[rec] = i;
-    const int sq = B.hcnt[i];
     cur.seq[rec] = sq;
     B.hcnt[i] = sq + 1;
   } else {
     atomicOr(err, kErrHistory);
   }
-  Corrected out;
-  out.d_old = d;
-  out.underflow = 0;
-  if (pass == 0) {
-    out.d_new = forward_step(tn, d, dts, P.k_min, P.k_max, &out.underflow);
-  } else {
-    // advance the body's previous-pass cursor to the block time; the
-    // lookups below then read the few records that follow it
-    int start = B.cursor[i];
-    const int end = B.hoff[i + 1];
-    if (prev.tau[start] <= tn) {
-      while (start + 1 < end && prev.tau[start + 1] <= tn) ++start;
-      B.cursor[i] = start;
-    }
-    const double e2 = history_dts_at(prev, start, end, tn + 2 * d, dts);
-    const double e1 = history_dts_at(prev, start, end, tn + d, dts);
-    out.d_new = symmetric_step(tn, d, dts, e2, e1, P.k_min, P.k_max,
-                               P.dtmax_t, &out.underflow);
-  }
+  if (new_cursor >= 0) B.cursor[i] = new_cursor;
   B.dt[i] = out.d_new;
   return out;
 }
