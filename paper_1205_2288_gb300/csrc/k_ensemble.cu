@@ -107,14 +107,18 @@ __global__ void ens_predict_kernel(Bodies B, Params P, Ens E, History prev) {
   bool act = false;
   int c = -1;
   if (j < B.n) {
+    // the body's inputs are loaded alongside its cluster's block time
     c = E.cl[j];
+    const long long tj = B.tau[j];
+    const long long dtj = B.dt[j];
+    PredIn L;
+    load_pred_in(B, j, pass > 0, L);
     const long long tn = E.tau_next[c];
     if (tn != LLONG_MAX) {
-      const long long tj = B.tau[j];
-      const long long nt = tj + B.dt[j];
+      const long long nt = tj + dtj;
       act = (nt == tn);
       if (nt < tn) atomicOr(&ctl->err, kErrInvariant);
-      predict_body(B, P, prev, j, tj, tn, pass, act);
+      predict_body(B, P, prev, j, tj, tn, pass, act, L);
     }
   }
   // lanes of one cluster share one atomic on the cluster's counter

@@ -77,6 +77,16 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
   __shared__ long long s_tn;
   __shared__ int s_stop;
   Ctl* ctl = P.ctl;
+  // this body's inputs, loaded before the block time is known
+  const int pass = ctl->pass;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  long long tj = 0, dtj = 0;
+  PredIn L;
+  if (j < B.n) {
+    tj = B.tau[j];
+    dtj = B.dt[j];
+    load_pred_in(B, j, pass > 0, L);
+  }
   if (threadIdx.x < 32) {
     // smallest populated step = highest populated level, one warp-wide load
     const int lane = threadIdx.x;
@@ -110,16 +120,13 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
   }
   const long long tn = s_tn;
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->slot[p].tau_next = tn;
-  const int pass = ctl->pass;
   const History& prev = HB;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = false;
   if (j < B.n) {
-    const long long tj = B.tau[j];
-    const long long nt = tj + B.dt[j];
+    const long long nt = tj + dtj;
     act = (nt == tn);
     if (nt < tn) atomicOr(&ctl->err, kErrInvariant);
-    predict_body(B, P, prev, j, tj, tn, pass, act);
+    predict_body(B, P, prev, j, tj, tn, pass, act, L);
   }
   // compaction of the active list (order within a step is arbitrary)
   const unsigned bal = __ballot_sync(kFull, act);

@@ -32,21 +32,47 @@ __device__ __forceinline__ void store_prediction(const Bodies& B,
   }
 }
 
+// Body j's prediction inputs, loaded in one batch before the block time is
+// known: its state (for Eq. 2) and its segment cache (the previous-pass
+// records bracketing the last block time: times ta, tb and r, v, a of both
+// ends, 18 values).
+struct PredIn {
+  double r[3], v[3], a[3];
+  long long ta, tb;
+  double seg[18];
+};
+
+__device__ __forceinline__ void load_pred_in(const Bodies& B, int j,
+                                             bool with_seg, PredIn& L) {
+  for (int d = 0; d < 3; ++d) {
+    L.r[d] = B.r[d][j];
+    L.v[d] = B.v[d][j];
+    L.a[d] = B.a[d][j];
+  }
+  if (with_seg) {
+    const int n = B.n;
+    L.ta = B.seg_ta[j];
+    L.tb = B.seg_tb[j];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) L.seg[q] = B.seg[(long long)q * n + j];
+  }
+}
+
 // Body j (time tj) at block time tn: Taylor (Eq. 2) in the first pass and
 // for active bodies; otherwise cubic Hermite between the previous pass's
 // records that bracket tn, the record itself on an exact hit, Taylor where
 // the records do not reach tn. The bracketing records are kept in the
 // body's segment cache and refilled from its contiguous (CSR) records when
-// tn leaves the segment.
+// tn leaves the segment. L holds the body's preloaded inputs.
 __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
                                              const History& prev, int j,
                                              long long tj, long long tn,
-                                             int pass, bool act) {
+                                             int pass, bool act, PredIn& L) {
   double rp[3], vp[3];
   bool have = false;
   if (pass > 0 && !act) {
     const int n = B.n;
-    long long ta = B.seg_ta[j], tb = B.seg_tb[j];
+    long long ta = L.ta, tb = L.tb;
     if (!(ta <= tn && (tb < 0 || tn < tb))) {
       int c = B.cursor[j];
       const int end = B.hoff[j + 1];
@@ -57,15 +83,17 @@ __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
         ta = prev.tau[c];
         tb = nx >= 0 ? prev.tau[nx] : -1;
         for (int d = 0; d < 3; ++d) {
-          B.seg[(d + 0) * n + j] = prev.r[d][c];
-          B.seg[(d + 3) * n + j] = prev.v[d][c];
-          B.seg[(d + 6) * n + j] = prev.a[d][c];
+          L.seg[d + 0] = prev.r[d][c];
+          L.seg[d + 3] = prev.v[d][c];
+          L.seg[d + 6] = prev.a[d][c];
           if (nx >= 0) {
-            B.seg[(d + 9) * n + j] = prev.r[d][nx];
-            B.seg[(d + 12) * n + j] = prev.v[d][nx];
-            B.seg[(d + 15) * n + j] = prev.a[d][nx];
+            L.seg[d + 9] = prev.r[d][nx];
+            L.seg[d + 12] = prev.v[d][nx];
+            L.seg[d + 15] = prev.a[d][nx];
           }
         }
+#pragma unroll
+        for (int q = 0; q < 18; ++q) B.seg[(long long)q * n + j] = L.seg[q];
       } else {
         ta = LLONG_MAX;  // no record at or before tn: Taylor
         tb = -1;
@@ -75,25 +103,24 @@ __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
     }
     if (ta == tn) {
       for (int d = 0; d < 3; ++d) {
-        rp[d] = B.seg[(d + 0) * n + j];
-        vp[d] = B.seg[(d + 3) * n + j];
+        rp[d] = L.seg[d + 0];
+        vp[d] = L.seg[d + 3];
       }
       have = true;
     } else if (ta < tn && tb > tn) {
       const HermiteW w = hermite_weights(ta, tb, tn, P.inv_ticks);
       for (int d = 0; d < 3; ++d) {
-        rp[d] = hermite1(w, B.seg[(d + 0) * n + j], B.seg[(d + 3) * n + j],
-                         B.seg[(d + 9) * n + j], B.seg[(d + 12) * n + j]);
-        vp[d] = hermite1(w, B.seg[(d + 3) * n + j], B.seg[(d + 6) * n + j],
-                         B.seg[(d + 12) * n + j], B.seg[(d + 15) * n + j]);
+        rp[d] = hermite1(w, L.seg[d + 0], L.seg[d + 3], L.seg[d + 9],
+                         L.seg[d + 12]);
+        vp[d] = hermite1(w, L.seg[d + 3], L.seg[d + 6], L.seg[d + 12],
+                         L.seg[d + 15]);
       }
       have = true;
     }
   }
   if (!have) {
     const double h = __dmul_rn((double)(tn - tj), P.inv_ticks);
-    for (int d = 0; d < 3; ++d)
-      taylor1(B.r[d][j], B.v[d][j], B.a[d][j], h, rp[d], vp[d]);
+    for (int d = 0; d < 3; ++d) taylor1(L.r[d], L.v[d], L.a[d], h, rp[d], vp[d]);
   }
   store_prediction(B, P, j, rp, vp);
 }
