@@ -107,12 +107,14 @@ __global__ void ens_predict_kernel(Bodies B, Params P, Ens E, History prev) {
   bool act = false;
   int c = -1;
   if (j < B.n) {
-    // the body's inputs are loaded alongside its cluster's block time
+    // the body's time and step are loaded alongside its cluster's block
+    // time; the prediction reads the rest as its path needs it
     c = E.cl[j];
     const long long tj = B.tau[j];
     const long long dtj = B.dt[j];
     PredIn L;
-    load_pred_in(B, j, pass > 0, L);
+    L.have_state = false;
+    L.have_seg = false;
     const long long tn = E.tau_next[c];
     if (tn != LLONG_MAX) {
       const long long nt = tj + dtj;

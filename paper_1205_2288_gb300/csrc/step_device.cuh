@@ -36,26 +36,41 @@ __device__ __forceinline__ void store_prediction(const Bodies& B,
 // known: its state (for Eq. 2) and its segment cache (the previous-pass
 // records bracketing the last block time: times ta, tb and r, v, a of both
 // ends, 18 values).
+// Fields not preloaded (have_state / have_seg false) are read by
+// predict_body when its path needs them, which keeps the memory traffic of
+// very large body counts (ensembles) at what each path reads.
 struct PredIn {
   double r[3], v[3], a[3];
   long long ta, tb;
   double seg[18];
+  bool have_state, have_seg;
 };
 
-__device__ __forceinline__ void load_pred_in(const Bodies& B, int j,
-                                             bool with_seg, PredIn& L) {
+__device__ __forceinline__ void load_pred_state(const Bodies& B, int j,
+                                                PredIn& L) {
   for (int d = 0; d < 3; ++d) {
     L.r[d] = B.r[d][j];
     L.v[d] = B.v[d][j];
     L.a[d] = B.a[d][j];
   }
-  if (with_seg) {
-    const int n = B.n;
-    L.ta = B.seg_ta[j];
-    L.tb = B.seg_tb[j];
+  L.have_state = true;
+}
+
+__device__ __forceinline__ void load_pred_seg(const Bodies& B, int j,
+                                              PredIn& L) {
+  const int n = B.n;
+  L.ta = B.seg_ta[j];
+  L.tb = B.seg_tb[j];
 #pragma unroll
-    for (int q = 0; q < 18; ++q) L.seg[q] = B.seg[(long long)q * n + j];
-  }
+  for (int q = 0; q < 18; ++q) L.seg[q] = B.seg[(long long)q * n + j];
+  L.have_seg = true;
+}
+
+__device__ __forceinline__ void load_pred_in(const Bodies& B, int j,
+                                             bool with_seg, PredIn& L) {
+  load_pred_state(B, j, L);
+  L.have_seg = false;
+  if (with_seg) load_pred_seg(B, j, L);
 }
 
 // Body j (time tj) at block time tn: Taylor (Eq. 2) in the first pass and
@@ -72,6 +87,7 @@ __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
   bool have = false;
   if (pass > 0 && !act) {
     const int n = B.n;
+    if (!L.have_seg) load_pred_seg(B, j, L);
     long long ta = L.ta, tb = L.tb;
     if (!(ta <= tn && (tb < 0 || tn < tb))) {
       int c = B.cursor[j];
@@ -119,6 +135,7 @@ __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
     }
   }
   if (!have) {
+    if (!L.have_state) load_pred_state(B, j, L);
     const double h = __dmul_rn((double)(tn - tj), P.inv_ticks);
     for (int d = 0; d < 3; ++d) taylor1(L.r[d], L.v[d], L.a[d], h, rp[d], vp[d]);
   }
