@@ -89,6 +89,12 @@ def lib():
             L.orc_destroy.argtypes = [C.c_void_p]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
+            L.orc_hist_find.argtypes = [I64, I64P, I64]
+            L.orc_hist_find.restype = I64
+            L.orc_hist_dts_at.argtypes = [I64, I64P, DP, I64, C.c_double]
+            L.orc_hist_dts_at.restype = C.c_double
+            L.orc_predict_prev.argtypes = [I64, I64P, DP, DP, DP, I64, DP, DP,
+                                           DP, I64, C.c_int, DP, DP]
             sched = [I64, I64P, I64P, I32P]
             L.orc_replay.argtypes = [I64, DP, DP, DP, C.c_double, C.c_int,
                                      *sched, DP, DP]
@@ -165,6 +171,32 @@ def hermite(ta, tb, t, k_max, ra, va, aa, rb, vb, ab):
     lib().orc_hermite(int(ta), int(tb), int(t), int(k_max),
                       *[_p(x) for x in args], _p(ro), _p(vo))
     return ro, vo
+
+
+def hist_find(tau, t):
+    """Index of the last record with tau <= t, or -1 (R6)."""
+    tau = np.ascontiguousarray(tau, dtype=np.int64)
+    return int(lib().orc_hist_find(tau.shape[0], _p(tau, I64P), int(t)))
+
+
+def hist_dts_at(tau, dts, t, fallback):
+    """Previous pass's step estimate at tick t (R8)."""
+    tau = np.ascontiguousarray(tau, dtype=np.int64)
+    dts = _d(dts)
+    return float(lib().orc_hist_dts_at(tau.shape[0], _p(tau, I64P), _p(dts),
+                                       int(t), float(fallback)))
+
+
+def predict_prev(tau, r, v, a, tj, rj, vj, aj, tn, k_max):
+    """Prediction of a non-active body in a pass >= 1 (R6)."""
+    tau = np.ascontiguousarray(tau, dtype=np.int64)
+    r, v, a = _d(r), _d(v), _d(a)
+    rj, vj, aj = _d(rj), _d(vj), _d(aj)
+    rp, vp = np.zeros(3), np.zeros(3)
+    lib().orc_predict_prev(tau.shape[0], _p(tau, I64P), _p(r), _p(v), _p(a),
+                           int(tj), _p(rj), _p(vj), _p(aj), int(tn),
+                           int(k_max), _p(rp), _p(vp))
+    return rp, vp
 
 
 def final_pass(sched, era=-1):

@@ -37,6 +37,12 @@
  *  R10 Steps below 2^-k_max are clamped to 2^-k_max and counted.
  *  R11 Dynamic era = last block time - first block time, clamped to
  *      [dt_max 2^-dyn_min_log2, dt_max] and rounded down to a power of two.
+ *
+ * Pins: the record lookup, R8's estimate and R6's prediction are pinned
+ * through the exported hooks orc_hist_find, orc_hist_dts_at and
+ * orc_predict_prev. Parity unpinned: whether passes >= 1 interpolate at
+ * all (the call site in run_pass) has no observable beyond the scheme's
+ * own error.
  */
 #include "tsbts_oracle.h"
 
@@ -294,6 +300,69 @@ static double ticks_to_time(int64_t t, int k_max) {
   return ldexp((double)t, -k_max);
 }
 
+/* R6 for a body that is not active in a pass >= 1: its previous-pass
+ * record at tn on an exact hit, else the cubic Hermite between the records
+ * bracketing tn, else (tn before the first or after the last record) Eq. 2
+ * from the body's own state (r, v, a at tick tj). */
+static void predict_prev(const history* hp, int64_t tj, const double* r,
+                         const double* v, const double* a, int64_t tn,
+                         int k_max, double* rp, double* vp) {
+  const int64_t k = hist_find(hp, tn);
+  if (k >= 0 && hp->rec[k].tau == tn) {
+    memcpy(rp, hp->rec[k].r, sizeof(double) * 3);
+    memcpy(vp, hp->rec[k].v, sizeof(double) * 3);
+  } else if (k >= 0 && k + 1 < hp->len) {
+    const record* A = &hp->rec[k];
+    const record* B = &hp->rec[k + 1];
+    orc_hermite(A->tau, B->tau, tn, k_max, A->r, A->v, A->a, B->r, B->v,
+                B->a, rp, vp);
+  } else {
+    taylor(r, v, a, ticks_to_time(tn - tj, k_max), rp, vp);
+  }
+}
+
+/* one body's previous-pass records from arrays (tau[len] ascending;
+ * r, v, a as (len, 3); dts may be NULL) */
+static history hist_of(int64_t len, const int64_t* tau, const double* r,
+                       const double* v, const double* a, const double* dts) {
+  history h = {0, 0, 0};
+  for (int64_t k = 0; k < len; ++k) {
+    record x;
+    memset(&x, 0, sizeof x);
+    x.tau = tau[k];
+    if (r) memcpy(x.r, r + 3 * k, sizeof x.r);
+    if (v) memcpy(x.v, v + 3 * k, sizeof x.v);
+    if (a) memcpy(x.a, a + 3 * k, sizeof x.a);
+    x.dts = dts ? dts[k] : 0.0;
+    hist_push(&h, &x);
+  }
+  return h;
+}
+
+int64_t orc_hist_find(int64_t len, const int64_t* tau, int64_t t) {
+  history h = hist_of(len, tau, NULL, NULL, NULL, NULL);
+  const int64_t k = hist_find(&h, t);
+  free(h.rec);
+  return k;
+}
+
+double orc_hist_dts_at(int64_t len, const int64_t* tau, const double* dts,
+                       int64_t t, double fallback) {
+  history h = hist_of(len, tau, NULL, NULL, NULL, dts);
+  const double e = hist_dts_at(&h, t, fallback);
+  free(h.rec);
+  return e;
+}
+
+void orc_predict_prev(int64_t len, const int64_t* tau, const double* r,
+                      const double* v, const double* a, int64_t tj,
+                      const double* rj, const double* vj, const double* aj,
+                      int64_t tn, int k_max, double* rp, double* vp) {
+  history h = hist_of(len, tau, r, v, a, NULL);
+  predict_prev(&h, tj, rj, vj, aj, tn, k_max, rp, vp);
+  free(h.rec);
+}
+
 orc_sim* orc_create(int64_t n, const double* m, const double* r,
                     const double* v, const orc_cfg* cfg) {
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
@@ -389,17 +458,9 @@ static void run_pass(orc_sim* s, int era_idx, int pass, int64_t tau_e) {
     /* Alg. 2 step 4: predict or interpolate every body to tn (R6) */
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
-      const history* hp = &s->hprev[j];
-      int64_t k = -1;
-      if (pass > 0 && !s->is_act[j]) k = hist_find(hp, tn);
-      if (k >= 0 && hp->rec[k].tau == tn) {
-        memcpy(s->rp + 3 * j, hp->rec[k].r, sizeof(double) * 3);
-        memcpy(s->vp + 3 * j, hp->rec[k].v, sizeof(double) * 3);
-      } else if (k >= 0 && k + 1 < hp->len) {
-        const record* A = &hp->rec[k];
-        const record* B = &hp->rec[k + 1];
-        orc_hermite(A->tau, B->tau, tn, k_max, A->r, A->v, A->a, B->r, B->v,
-                    B->a, s->rp + 3 * j, s->vp + 3 * j);
+      if (pass > 0 && !s->is_act[j]) {
+        predict_prev(&s->hprev[j], s->tau[j], s->r + 3 * j, s->v + 3 * j,
+                     s->a + 3 * j, tn, k_max, s->rp + 3 * j, s->vp + 3 * j);
       } else {
         const double h = ticks_to_time(tn - s->tau[j], k_max);
         taylor(s->r + 3 * j, s->v + 3 * j, s->a + 3 * j, h, s->rp + 3 * j,

@@ -54,6 +54,22 @@ void orc_hermite(int64_t ta, int64_t tb, int64_t t, int k_max,
                  const double* rb, const double* vb, const double* ab,
                  double* r_out, double* v_out);
 
+/* One body's previous-pass records, given as arrays (tau[len] strictly
+ * ascending; r, v, a as (len, 3) rows), for the pins of readings R6 and
+ * R8: the index of the last record with tau <= t (-1 if none); the
+ * previous pass's step estimate at tick t (the record's on an exact hit,
+ * linear in time between two records, `fallback` before the first or
+ * after the last); and the prediction of a non-active body to tick tn in a
+ * pass >= 1 (the record on an exact hit, cubic Hermite between the
+ * bracketing records, else Eq. 2 from its own state rj, vj, aj at tj). */
+int64_t orc_hist_find(int64_t len, const int64_t* tau, int64_t t);
+double orc_hist_dts_at(int64_t len, const int64_t* tau, const double* dts,
+                       int64_t t, double fallback);
+void orc_predict_prev(int64_t len, const int64_t* tau, const double* r,
+                      const double* v, const double* a, int64_t tj,
+                      const double* rj, const double* vj, const double* aj,
+                      int64_t tn, int k_max, double* rp, double* vp);
+
 typedef struct {
   int n_iter;        /* passes per era (1 = plain block steps) */
   int era_mode;      /* 0 fixed, 1 dynamic */
