@@ -39,7 +39,7 @@ DT_MAX = 1.0 / 8.0
 T_END = 1.0
 N_ITER = 3
 SEED = 0
-SAMPLE_T = 2.0 ** -8        # oracle / FP64 sample interval
+SAMPLE_T = 2.0 ** -6        # oracle / FP64 sample interval (~16 s of oracle work)
 OPS_PER_INTERACTION = 20    # FMA-pipe ops of the algorithmic pair term
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
