@@ -268,10 +268,13 @@ typedef struct {
  * every step non-empty, each body at most once per step, each in [0, n)).
  * Arrays are copied. checkpoint_every = 0 tapes the pre-step state of
  * every entry during the forward replay (80 bytes per entry); K > 0 keeps
- * only a full-state checkpoint every K steps (80 bytes per body each) and
+ * only a full-state checkpoint every K steps (88 bytes per body each) and
  * recomputes each K-step segment, taped, during the reverse sweep.
  * Precision, k_max, exact_order, device and stream come from the context's
- * config. TSBTS_ERR_ARG: a bad size or schedule. */
+ * config; with graph_steps > 0 the whole forward replay and the whole
+ * reverse sweep are each captured once as a CUDA graph (on the first call)
+ * and replayed, with graph_steps = 0 every kernel is a stream launch.
+ * TSBTS_ERR_ARG: a bad size or schedule. */
 int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps,
                        int64_t n_steps, const int64_t* step_tau,
                        const int64_t* step_off, const int32_t* act,
