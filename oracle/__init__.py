@@ -35,7 +35,7 @@ class OrcCfg(C.Structure):
                 ("era_log2", C.c_int), ("k_max", C.c_int),
                 ("dyn_min_log2", C.c_int), ("log", C.c_int),
                 ("eps", C.c_double), ("eta", C.c_double),
-                ("dt_max", C.c_double)]
+                ("dt_max", C.c_double), ("conv_tol", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -270,12 +270,13 @@ class Sim:
     """One oracle integration (Alg. 2 / Alg. 3) over seeded inputs."""
 
     def __init__(self, m, r, v, *, eps, eta, dt_max, n_iter=3, era_mode=0,
-                 era_log2=3, k_max=20, dyn_min_log2=3, log=False):
+                 era_log2=3, k_max=20, dyn_min_log2=3, log=False,
+                 conv_tol=0.0):
         self.m, r, v = _d(m), _d(r), _d(v)
         self.n = self.m.shape[0]
         self.k_max = k_max
         cfg = OrcCfg(n_iter, era_mode, era_log2, k_max, dyn_min_log2,
-                     1 if log else 0, eps, eta, dt_max)
+                     1 if log else 0, eps, eta, dt_max, conv_tol)
         self._s = lib().orc_create(self.n, _p(self.m), _p(r), _p(v),
                                    C.byref(cfg))
 

@@ -247,8 +247,8 @@ struct orc_sim {
   int64_t dt_max_t;
   double *m, *r, *v, *a, *dts;
   int64_t *tau, *dt;
-  /* era-start snapshot */
-  double *r0, *v0, *a0, *dts0;
+  /* era-start snapshot; rlast: era-end positions of the previous pass */
+  double *r0, *v0, *a0, *dts0, *rlast;
   int64_t *tau0, *dt0;
   /* per-pass scratch */
   double *rp, *vp, *an, *phin, *qn;
@@ -382,6 +382,7 @@ orc_sim* orc_create(int64_t n, const double* m, const double* r,
   s->tau = xmalloc(ni);
   s->dt = xmalloc(ni);
   s->r0 = xmalloc(n3);
+  s->rlast = xmalloc(n3);
   s->v0 = xmalloc(n3);
   s->a0 = xmalloc(n3);
   s->dts0 = xmalloc(n1);
@@ -513,6 +514,23 @@ static void run_pass(orc_sim* s, int era_idx, int pass, int64_t tau_e) {
   }
 }
 
+/* Converged iteration: this pass took the same block steps as the
+ * previous one (every body's record times equal) and its era-end
+ * positions are within conv_tol of the previous pass's. */
+static int converged(const orc_sim* s) {
+  for (int64_t i = 0; i < s->n; ++i) {
+    const history* a = &s->hcur[i];
+    const history* b = &s->hprev[i];
+    if (a->len != b->len) return 0;
+    for (int64_t k = 0; k < a->len; ++k)
+      if (a->rec[k].tau != b->rec[k].tau) return 0;
+    for (int c = 0; c < 3; ++c)
+      if (!(fabs(s->r[3 * i + c] - s->rlast[3 * i + c]) < s->cfg.conv_tol))
+        return 0;
+  }
+  return 1;
+}
+
 int orc_run(orc_sim* s, double t_end) {
   const int k_max = s->cfg.k_max;
   const double te = ldexp(t_end, k_max);
@@ -541,6 +559,7 @@ int orc_run(orc_sim* s, double t_end) {
     memcpy(s->dt0, s->dt, ni);
     for (int p = 0; p < s->cfg.n_iter; ++p) {
       if (p > 0) {
+        if (s->cfg.conv_tol > 0.0) memcpy(s->rlast, s->r, n3);
         /* Alg. 2 step 9: restart the era from its first block */
         memcpy(s->r, s->r0, n3);
         memcpy(s->v, s->v0, n3);
@@ -554,6 +573,7 @@ int orc_run(orc_sim* s, double t_end) {
       }
       run_pass(s, era_idx, p, tau_e);
       s->stats[3] += 1;
+      if (p > 0 && s->cfg.conv_tol > 0.0 && converged(s)) break;
     }
     s->t_sys = tau_e;
     s->stats[2] += 1;
@@ -628,7 +648,7 @@ void orc_destroy(orc_sim* s) {
   free(s->hcur);
   free(s->m); free(s->r); free(s->v); free(s->a); free(s->dts);
   free(s->tau); free(s->dt);
-  free(s->r0); free(s->v0); free(s->a0); free(s->dts0);
+  free(s->r0); free(s->rlast); free(s->v0); free(s->a0); free(s->dts0);
   free(s->tau0); free(s->dt0);
   free(s->rp); free(s->vp); free(s->an); free(s->phin); free(s->qn);
   free(s->act); free(s->is_act);

@@ -78,6 +78,12 @@ typedef struct {
   int dyn_min_log2;  /* dynamic era lower limit = dt_max * 2^-dyn_min_log2 */
   int log;           /* record the block schedule */
   double eps, eta, dt_max;
+  double conv_tol;   /* > 0: converged iteration — after pass p >= 1 the
+                        era stops when every body's record times equal the
+                        previous pass's (same block schedule) and every
+                        era-end position differs from the previous pass's
+                        by less than conv_tol; n_iter is then the upper
+                        bound. 0: always n_iter passes. */
 } orc_cfg;
 
 typedef struct orc_sim orc_sim;
