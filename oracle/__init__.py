@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tsbts_oracle.c")
 _SRC_ADJ = os.path.join(_HERE, "tsbts_adjoint.c")
+_SRC_ERA = os.path.join(_HERE, "tsbts_adjoint_era.c")
 _HDR = os.path.join(_HERE, "tsbts_oracle.h")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _SO = os.path.join(_LIBDIR, "liboracle.so")
@@ -41,13 +42,14 @@ class OrcCfg(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, OpenMP over bodies)."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    newest = max(os.path.getmtime(x) for x in (_SRC, _SRC_ADJ, _HDR))
+    newest = max(os.path.getmtime(x) for x in (_SRC, _SRC_ADJ, _SRC_ERA,
+                                               _HDR))
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
            "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, _SRC_ADJ,
-           "-lm"]
+           _SRC_ERA, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -100,6 +102,12 @@ def lib():
                                      *sched, DP, DP]
             L.orc_replay_vjp.argtypes = [I64, DP, DP, DP, C.c_double, C.c_int,
                                          *sched, DP, DP, DP, DP, DP]
+            era = [I64, I64P, I64P, I64P, I32P]
+            L.orc_era_replay.argtypes = [I64, DP, DP, DP, C.c_double,
+                                         C.c_int, *era, DP, DP]
+            L.orc_era_replay_vjp.argtypes = [I64, DP, DP, DP, C.c_double,
+                                             C.c_int, *era, DP, DP, DP, DP,
+                                             DP]
             L.orc_loss_msr.argtypes = [I64, DP, DP, DP, DP]
             L.orc_loss_msr.restype = C.c_double
             _lib = L
@@ -245,6 +253,59 @@ def replay_vjp(m, r0, v0, eps, k_max, schedule, gr_T, gv_T):
     lib().orc_replay_vjp(m.shape[0], _p(m), _p(r0), _p(v0), float(eps),
                          int(k_max), *sa, _p(gr_T), _p(gv_T), _p(g_r0),
                          _p(g_v0), _p(g_m))
+    return g_r0, g_v0, g_m
+
+
+def era_passes(sched, era=0):
+    """Every pass of one era from a schedule log: a list of
+    (step_tau, step_off, act) per pass, active bodies ascending per step."""
+    off = np.concatenate([[0], np.cumsum(sched["n_act"])]).astype(np.int64)
+    sel = np.flatnonzero(sched["era"] == np.unique(sched["era"])[era])
+    out = []
+    for p in np.unique(sched["pass_"][sel]):
+        steps = sel[sched["pass_"][sel] == p]
+        parts = [np.sort(sched["idx"][off[k]:off[k + 1]]) for k in steps]
+        so = np.concatenate([[0], np.cumsum([len(x) for x in parts])])
+        out.append((sched["tau"][steps].astype(np.int64), so.astype(np.int64),
+                    np.concatenate(parts).astype(np.int32)))
+    return out
+
+
+def _era_args(passes):
+    tau = np.concatenate([p[0] for p in passes]).astype(np.int64)
+    pass_off = np.concatenate([[0], np.cumsum([len(p[0]) for p in passes])])
+    offs, base = [], 0
+    for i, p in enumerate(passes):
+        o = np.asarray(p[1], np.int64) + base
+        offs.append(o if i == len(passes) - 1 else o[:-1])
+        base = int(o[-1])
+    step_off = np.concatenate(offs).astype(np.int64)
+    act = np.concatenate([p[2] for p in passes]).astype(np.int32)
+    pass_off = np.ascontiguousarray(pass_off, dtype=np.int64)
+    keep = (tau, pass_off, step_off, act)
+    return keep, [len(passes), _p(pass_off, I64P), _p(tau, I64P),
+                  _p(step_off, I64P), _p(act, I32P)]
+
+
+def era_replay(m, r0, v0, eps, k_max, passes):
+    """Last pass's final (r, v) of the multi-pass era replay."""
+    m, r0, v0 = _d(m), _d(r0), _d(v0)
+    keep, ea = _era_args(passes)
+    r, v = np.zeros_like(r0), np.zeros_like(v0)
+    lib().orc_era_replay(m.shape[0], _p(m), _p(r0), _p(v0), float(eps),
+                         int(k_max), *ea, _p(r), _p(v))
+    return r, v
+
+
+def era_replay_vjp(m, r0, v0, eps, k_max, passes, gr_T, gv_T):
+    """Cotangents (g_r0, g_v0, g_m) through every pass of the era."""
+    m, r0, v0 = _d(m), _d(r0), _d(v0)
+    gr_T, gv_T = _d(gr_T), _d(gv_T)
+    keep, ea = _era_args(passes)
+    g_r0, g_v0, g_m = np.zeros_like(r0), np.zeros_like(v0), np.zeros_like(m)
+    lib().orc_era_replay_vjp(m.shape[0], _p(m), _p(r0), _p(v0), float(eps),
+                             int(k_max), *ea, _p(gr_T), _p(gv_T), _p(g_r0),
+                             _p(g_v0), _p(g_m))
     return g_r0, g_v0, g_m
 
 

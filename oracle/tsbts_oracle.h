@@ -141,6 +141,29 @@ void orc_replay_vjp(int64_t n, const double* m, const double* r0,
                     const int32_t* act, const double* gr_T, const double* gv_T,
                     double* g_r0, double* g_v0, double* g_m);
 
+/* The adjoint through every pass of one era (reading R14 extended to the
+ * symmetrised passes): the era's n_pass passes are replayed on their
+ * frozen schedules, each from (r0, v0) at tick 0 with a0 = the force at
+ * r0, with Eq. 2 prediction in the first pass and for active bodies and
+ * the previous pass's records (R6) for the others in passes >= 1, as the
+ * integrator runs them. Pass p's steps are pass_off[p] .. pass_off[p+1]-1
+ * of step_tau and step_off (entry offsets into act, not restarting per
+ * pass). orc_era_replay gives the last pass's final state;
+ * orc_era_replay_vjp the cotangents of r0, v0 and m for cotangents gr_T,
+ * gv_T of that state, through every pass and its records. */
+void orc_era_replay(int64_t n, const double* m, const double* r0,
+                    const double* v0, double eps, int k_max, int64_t n_pass,
+                    const int64_t* pass_off, const int64_t* step_tau,
+                    const int64_t* step_off, const int32_t* act,
+                    double* r_out, double* v_out);
+void orc_era_replay_vjp(int64_t n, const double* m, const double* r0,
+                        const double* v0, double eps, int k_max,
+                        int64_t n_pass, const int64_t* pass_off,
+                        const int64_t* step_tau, const int64_t* step_off,
+                        const int32_t* act, const double* gr_T,
+                        const double* gv_T, double* g_r0, double* g_v0,
+                        double* g_m);
+
 /* Mass-weighted mean-square radius about the origin,
  * L = sum_i m_i |r_i|^2 / sum_i m_i, with its partial derivatives with
  * respect to r (g_r) and m (g_m); either may be NULL. */
