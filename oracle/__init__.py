@@ -79,6 +79,9 @@ def lib():
             L.orc_run.restype = C.c_int
             L.orc_energy.argtypes = [C.c_void_p, DP, DP]
             L.orc_get_state.argtypes = [C.c_void_p, DP, DP, DP, I64P, I64P, DP]
+            L.orc_set_state.argtypes = [C.c_void_p, I64, DP, DP, DP, DP, I64P,
+                                        I64P, DP]
+            L.orc_set_state.restype = C.c_int
             L.orc_stats.argtypes = [C.c_void_p, I64P]
             L.orc_log_steps.argtypes = [C.c_void_p]
             L.orc_log_steps.restype = I64
@@ -359,6 +362,26 @@ class Sim:
         lib().orc_get_state(self._s, _p(r), _p(v), _p(a), _p(tau, I64P),
                             _p(dt, I64P), _p(dts))
         return dict(r=r, v=v, a=a, tau=tau, dt=dt, dts=dts)
+
+    def set_state(self, t, m, st):
+        """Resume at an era end: system time t (time units, a whole number
+        of ticks), masses m and the fields of state() (r, v, a, tau, dt,
+        dts). Raises ValueError (state unchanged) when the state could not
+        end an era."""
+        tt = float(t) * 2.0 ** self.k_max
+        if tt != np.floor(tt):
+            raise ValueError("t is not a whole number of ticks")
+        n = self.n
+        m = _d(m).reshape(n)
+        r, v, a = (_d(st[k]).reshape(n, 3) for k in ("r", "v", "a"))
+        tau = np.ascontiguousarray(st["tau"], np.int64).reshape(n)
+        dt = np.ascontiguousarray(st["dt"], np.int64).reshape(n)
+        dts = _d(st["dts"]).reshape(n)
+        rc = lib().orc_set_state(self._s, int(tt), _p(m), _p(r), _p(v), _p(a),
+                                 _p(tau, I64P), _p(dt, I64P), _p(dts))
+        if rc != 0:
+            raise ValueError("state cannot end an era")
+        self.m = m.copy()
 
     def stats(self):
         out = np.zeros(7, np.int64)

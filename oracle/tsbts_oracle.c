@@ -606,6 +606,43 @@ void orc_get_state(orc_sim* s, double* r, double* v, double* a, int64_t* tau,
   if (dts) memcpy(dts, s->dts, sizeof(double) * (size_t)n);
 }
 
+/* Resume at an era end. An era starts from (m, r, v, a, dts, tau, dt) and
+ * the system time alone: its first pass predicts with Eq. 2 only and every
+ * later pass interpolates records of the same era (Alg. 2 steps 2-9), so
+ * these fields are the whole state carried from one era to the next. A
+ * state is accepted when it could end an era: every step a power of two
+ * within [1, dt_max], every body time a multiple of its step, tau <= t <
+ * tau + dt, finite masses and vectors, dts > 0 (+inf allowed: a body that
+ * feels no force). */
+int orc_set_state(orc_sim* s, int64_t t, const double* m, const double* r,
+                  const double* v, const double* a, const int64_t* tau,
+                  const int64_t* dt, const double* dts) {
+  const int64_t n = s->n;
+  if (t < 0) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t d = dt[i];
+    if (d < 1 || d > s->dt_max_t || (d & (d - 1)) != 0) return -1;
+    if (tau[i] < 0 || tau[i] % d != 0 || tau[i] > t || tau[i] + d <= t)
+      return -1;
+    if (!isfinite(m[i]) || !(dts[i] > 0.0)) return -1;
+    for (int c = 0; c < 3; ++c)
+      if (!isfinite(r[3 * i + c]) || !isfinite(v[3 * i + c]) ||
+          !isfinite(a[3 * i + c]))
+        return -1;
+  }
+  const size_t n3 = sizeof(double) * 3 * (size_t)n, n1 = sizeof(double) * (size_t)n;
+  const size_t ni = sizeof(int64_t) * (size_t)n;
+  memcpy(s->m, m, n1);
+  memcpy(s->r, r, n3);
+  memcpy(s->v, v, n3);
+  memcpy(s->a, a, n3);
+  memcpy(s->tau, tau, ni);
+  memcpy(s->dt, dt, ni);
+  memcpy(s->dts, dts, n1);
+  s->t_sys = t;
+  return 0;
+}
+
 void orc_stats(orc_sim* s, int64_t* out) {
   s->stats[5] = s->t_sys;
   memcpy(out, s->stats, sizeof s->stats);

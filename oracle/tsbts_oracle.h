@@ -97,6 +97,14 @@ int orc_run(orc_sim* s, double t_end);
 void orc_energy(orc_sim* s, double* ekin, double* epot);
 void orc_get_state(orc_sim* s, double* r, double* v, double* a, int64_t* tau,
                    int64_t* dt, double* dts);
+/* Replace the state with one that ends an era at system time t (ticks):
+ * masses, r, v, a at each body's own time tau, steps dt (ticks) and step
+ * estimates dts. Returns 0, or -1 (nothing changed) when the state could not
+ * end an era: a step not a power of two in [1, dt_max], tau not a multiple
+ * of dt, not tau <= t < tau + dt, a non-finite value, or dts <= 0. */
+int orc_set_state(orc_sim* s, int64_t t, const double* m, const double* r,
+                  const double* v, const double* a, const int64_t* tau,
+                  const int64_t* dt, const double* dts);
 /* stats: [0] block steps, [1] interactions (sum n_act * n), [2] eras,
  * [3] passes, [4] step underflows, [5] system time in ticks,
  * [6] initial interactions */
