@@ -154,6 +154,29 @@ int tsbts_energy(tsbts_ctx* ctx, double* ekin, double* epot, double* etot);
 int tsbts_state(tsbts_ctx* ctx, double* t, double* m, double* r, double* v,
                 double* a, int64_t* tau_ticks, int64_t* dt_ticks);
 
+/* Copy each body's step estimate (Eq. 3 with Plummer softening: eta over
+ * the square root of the time-step criterion, at the body's own time) to
+ * the HOST array dts[n]. With tsbts_state it forms a checkpoint. */
+int tsbts_step_estimates(tsbts_ctx* ctx, double* dts);
+
+/* Resume at an era end (Alg. 2 steps 2 and 10: an era starts from the
+ * bodies' m, r, v, a, step estimates, times and steps and the system time
+ * alone; its first pass uses Eq. 2 and later passes only records of the
+ * same era). HOST arrays as tsbts_state writes them, plus dts[n] from
+ * tsbts_step_estimates; t is the system time (a whole number of ticks).
+ * The context must hold a single system initialised with the same n;
+ * eps, eta and dt_max stay. A state saved at an era end of a run with the
+ * same configuration continues bit for bit like the uninterrupted run.
+ * TSBTS_ERR_ARG (nothing changed) unless every dt is a power of two in
+ * [1, dt_max] ticks, every tau a multiple of its dt with tau <= t <
+ * tau + dt, every value finite and every dts > 0 (+inf allowed);
+ * TSBTS_ERR_STATE for an ensemble. The arrays are read before the call
+ * returns. */
+int tsbts_set_state(tsbts_ctx* ctx, double t, const double* m,
+                    const double* r, const double* v, const double* a,
+                    const int64_t* tau_ticks, const int64_t* dt_ticks,
+                    const double* dts);
+
 int tsbts_get_stats(tsbts_ctx* ctx, tsbts_stats* out);
 
 /* Time every force launch with CUDA events (adds a small host cost per

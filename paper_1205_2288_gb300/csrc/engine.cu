@@ -841,6 +841,83 @@ int tsbts_state(tsbts_ctx* ctx, double* t, double* m, double* r, double* v,
   }
 }
 
+int tsbts_step_estimates(tsbts_ctx* ctx, double* dts) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (!dts) return fail(ctx, TSBTS_ERR_ARG, "null output pointer");
+  try {
+    ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+    ck(cudaMemcpyAsync(dts, ctx->B.dts, sizeof(double) * ctx->n,
+                       cudaMemcpyDeviceToHost, ctx->s), "read dts");
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
+int tsbts_set_state(tsbts_ctx* ctx, double t, const double* m,
+                    const double* r, const double* v, const double* a,
+                    const int64_t* tau_ticks, const int64_t* dt_ticks,
+                    const double* dts) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (ctx->ensemble)
+    return fail(ctx, TSBTS_ERR_STATE, "set_state takes a single system");
+  if (!m || !r || !v || !a || !tau_ticks || !dt_ticks || !dts)
+    return fail(ctx, TSBTS_ERR_ARG, "null state pointer");
+  const double tt = std::ldexp(t, ctx->cfg.k_max);
+  if (!std::isfinite(tt) || tt != std::floor(tt) || tt < 0.0 || tt > 9.0e18)
+    return fail(ctx, TSBTS_ERR_ARG, "t must be a whole number of ticks >= 0");
+  const long long T = (long long)tt;
+  const int n = ctx->n;
+  // a state that could end an era; every step indexes the level histogram
+  for (int i = 0; i < n; ++i) {
+    const long long d = dt_ticks[i], ti = tau_ticks[i];
+    bool ok = d >= 1 && d <= ctx->dtmax_t && (d & (d - 1)) == 0 && ti >= 0 &&
+              ti % d == 0 && ti <= T && T - ti < d;
+    ok = ok && std::isfinite(m[i]) && dts[i] > 0.0;
+    for (int c = 0; c < 3; ++c)
+      ok = ok && std::isfinite(r[3 * (size_t)i + c]) &&
+           std::isfinite(v[3 * (size_t)i + c]) &&
+           std::isfinite(a[3 * (size_t)i + c]);
+    if (!ok)
+      return fail(ctx, TSBTS_ERR_ARG,
+                  "state cannot end an era at body " + std::to_string(i));
+  }
+  try {
+    ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
+    // body-major host vectors to the per-component device arrays
+    std::vector<double> buf(9 * (size_t)n);
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c) {
+        buf[(size_t)c * n + i] = r[3 * (size_t)i + c];
+        buf[(size_t)(3 + c) * n + i] = v[3 * (size_t)i + c];
+        buf[(size_t)(6 + c) * n + i] = a[3 * (size_t)i + c];
+      }
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+      ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->s),
+         "copy state");
+    };
+    const size_t nd = sizeof(double) * n;
+    put(ctx->B.m, m, nd);
+    for (int c = 0; c < 3; ++c) {
+      put(ctx->B.r[c], buf.data() + (size_t)c * n, nd);
+      put(ctx->B.v[c], buf.data() + (size_t)(3 + c) * n, nd);
+      put(ctx->B.a[c], buf.data() + (size_t)(6 + c) * n, nd);
+    }
+    put(ctx->B.tau, tau_ticks, sizeof(long long) * n);
+    put(ctx->B.dt, dt_ticks, sizeof(long long) * n);
+    put(ctx->B.dts, dts, nd);
+    // the host buffers are read before the call returns
+    ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    ctx->t_sys = T;
+    return TSBTS_OK;
+  } catch (const CudaFail& f) {
+    return cuda_fail(ctx, f);
+  }
+}
+
 int tsbts_get_stats(tsbts_ctx* ctx, tsbts_stats* out) {
   int rc = check_ready(ctx);
   if (rc) return rc;

@@ -43,7 +43,7 @@ EXPORTS = (
     "tsbts_release_scratch", "tsbts_version", "tsbts_force_static",
     "tsbts_init_ensemble", "tsbts_ensemble_energy", "tsbts_adjoint_init",
     "tsbts_adjoint_forward", "tsbts_adjoint_vjp", "tsbts_adjoint_loss_grad",
-    "tsbts_adjoint_get_stats",
+    "tsbts_adjoint_get_stats", "tsbts_step_estimates", "tsbts_set_state",
 )
 
 
@@ -112,6 +112,9 @@ def lib():
         L.tsbts_step_era.argtypes = [VP, C.c_double, DP]
         L.tsbts_energy.argtypes = [VP, DP, DP, DP]
         L.tsbts_state.argtypes = [VP, DP, DP, DP, DP, DP, I64P, I64P]
+        L.tsbts_step_estimates.argtypes = [VP, DP]
+        L.tsbts_set_state.argtypes = [VP, C.c_double, DP, DP, DP, DP, I64P,
+                                      I64P, DP]
         L.tsbts_get_stats.argtypes = [VP, C.POINTER(tsbts_stats)]
         L.tsbts_set_timing.argtypes = [VP, C.c_int]
         L.tsbts_schedule_log.argtypes = [VP, I64]
@@ -229,6 +232,21 @@ def tsbts_state(ctx, n):
     _check(lib().tsbts_state(ctx, C.byref(t), _p(m), _p(r), _p(v), _p(a),
                              _p(tau, I64P), _p(dt, I64P)), ctx)
     return dict(t=t.value, m=m, r=r, v=v, a=a, tau=tau, dt=dt)
+
+
+def tsbts_step_estimates(ctx, n):
+    dts = np.zeros(n)
+    _check(lib().tsbts_step_estimates(ctx, _p(dts)), ctx)
+    return dts
+
+
+def tsbts_set_state(ctx, n, t, m, r, v, a, tau, dt, dts):
+    m, dts = (np.ascontiguousarray(x, np.float64).reshape(n) for x in (m, dts))
+    r, v, a = (np.ascontiguousarray(x, np.float64).reshape(n, 3)
+               for x in (r, v, a))
+    tau, dt = (np.ascontiguousarray(x, np.int64).reshape(n) for x in (tau, dt))
+    _check(lib().tsbts_set_state(ctx, float(t), _p(m), _p(r), _p(v), _p(a),
+                                 _p(tau, I64P), _p(dt, I64P), _p(dts)), ctx)
 
 
 def tsbts_get_stats(ctx) -> dict:
@@ -455,6 +473,19 @@ class Simulation:
 
     def state(self):
         return tsbts_state(self.ctx, self.n)
+
+    def checkpoint(self):
+        """The state at the system time with the step estimates: what
+        set_state needs to resume after an era end."""
+        st = tsbts_state(self.ctx, self.n)
+        st["dts"] = tsbts_step_estimates(self.ctx, self.n)
+        return st
+
+    def set_state(self, ck):
+        """Resume from checkpoint() taken at an era end of a run with the
+        same configuration and body count."""
+        tsbts_set_state(self.ctx, self.n, ck["t"], ck["m"], ck["r"], ck["v"],
+                        ck["a"], ck["tau"], ck["dt"], ck["dts"])
 
     def stats(self):
         return tsbts_get_stats(self.ctx)
