@@ -40,9 +40,11 @@
  *
  * Pins: the record lookup, R8's estimate and R6's prediction are pinned
  * through the exported hooks orc_hist_find, orc_hist_dts_at and
- * orc_predict_prev. Parity unpinned: whether passes >= 1 interpolate at
- * all (the call site in run_pass) has no observable beyond the scheme's
- * own error.
+ * orc_predict_prev. Parity partially unpinned: whether passes >= 1
+ * interpolate at all (the call site in run_pass) has no observable beyond
+ * the scheme's own error. Only the separately written multi-pass replay of
+ * tsbts_adjoint_era.c, a second restatement of the same reading, catches
+ * its omission.
  */
 #include "tsbts_oracle.h"
 
