@@ -36,3 +36,49 @@ def test_malformed_and_unavailable_samples_are_skipped():
         line(2070)])
     assert out["samples"] == 1 and out["sm_mhz"] == 2070
     assert bench.parse_clock_lines([])["sm_mhz"] is None
+
+
+def run_bench(*args, nproc=1):
+    import json
+    import socket
+    import subprocess
+    import sys
+    cmd = [sys.executable, bench.__file__]
+    if nproc > 1:
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               f"--nproc-per-node={nproc}", "--master-addr", "127.0.0.1",
+               "--master-port", str(port), bench.__file__]
+    p = subprocess.run(cmd + list(args), capture_output=True, text=True,
+                       timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm (the FP64 oracle on the host cores, a bounded
+    sample of the workload per step) needs no GPU."""
+    (line,) = run_bench("--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert line["impl"] == "reference"
+    for key in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data",
+                "config"):
+        assert key in line, key
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 0
+    assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["metric"] == bench.METRIC and line["higher_is_better"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_under_torchrun_prints_from_rank_0_only():
+    lines = run_bench("--impl", "reference", "--gpus", "2", "--steps", "1",
+                      "--warmup", "0", nproc=2)
+    assert len(lines) == 1
+    assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
