@@ -67,6 +67,9 @@ def test_resume_continues_bit_for_bit(case):
     tail = make(2 * m, r + rng.standard_normal(r.shape),
                 v - rng.standard_normal(v.shape), **kw)
     tail.set_state(t1, m, st)
+    back = tail.state()
+    for k in KEYS:
+        np.testing.assert_array_equal(back[k], st[k], err_msg=k)
     np.testing.assert_array_equal(tail.energy(), head.energy())
     tail.run(t2)
     a, b = full.state(), tail.state()
