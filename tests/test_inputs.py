@@ -42,6 +42,25 @@ def test_plummer_cumulative_mass_profile(big):
     assert stats.kstest(rad, cdf).pvalue > 1e-3
 
 
+def test_plummer_mass_cut(big):
+    """The radial mass fraction is cut at 0.999: no body lies beyond the
+    radius enclosing that fraction, and the shell between the radii
+    enclosing 0.99 and 0.999 holds its share (0.009 / 0.999) of the bodies,
+    which the cumulative profile alone does not resolve at this n."""
+    m, r, v = big
+    rad = np.linalg.norm(r, axis=1)
+
+    def radius_of(x):                  # inverse of the Plummer mass profile
+        return A / math.sqrt(x ** (-2.0 / 3.0) - 1.0)
+    # the move to the centre-of-mass frame is O(N^-1/2) of the rms radius
+    # (~0.01 here); 0.1 bounds it
+    assert rad.max() <= radius_of(CUT) + 0.1
+    n = rad.size
+    p = (CUT - 0.99) / CUT
+    outer = np.sum(rad > radius_of(0.99))
+    assert abs(outer - n * p) < 5 * math.sqrt(n * p * (1 - p)) + 2
+
+
 def test_plummer_speed_distribution_and_isotropy(big):
     m, r, v = big
     rad = np.linalg.norm(r, axis=1) / A           # Plummer units
