@@ -148,3 +148,39 @@ def test_energy_two_body_and_plummer(orc):
     assert abs(np.mean(ks) - 0.25) < 2.0 / math.sqrt(n)
     assert abs(np.mean(ws) + 0.5) < 2.0 / math.sqrt(n)
     assert abs(np.mean(2 * np.array(ks) / np.abs(ws)) - 1) < 4.0 / math.sqrt(n)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.05])
+def test_brute_force_in_forty_digits(orc, eps):
+    """The FP64 sums against the same sums in 40-digit arithmetic on the
+    exact values of the inputs (N = 48, unequal masses): a_i within 1e-14
+    of the scale of its terms, phi_i and q_i within 1e-14 relative."""
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp
+    mp.dps = 40
+    n = 48
+    m = inputs.salpeter_masses(n, 5)
+    _, r, v = inputs.plummer(n, 6, masses=m)
+    a, phi, q = orc.forces(m, r, v, eps)
+    M = [mp.mpf(float(x)) for x in m]
+    R = [[mp.mpf(float(x)) for x in row] for row in r]
+    V = [[mp.mpf(float(x)) for x in row] for row in v]
+    e2 = mp.mpf(eps) ** 2
+    for i in range(n):
+        ax, ph, qq, scale = [mp.mpf(0)] * 3, mp.mpf(0), mp.mpf(0), mp.mpf(0)
+        for j in range(n):
+            if j == i:
+                continue
+            d = [R[j][c] - R[i][c] for c in range(3)]
+            w = [V[j][c] - V[i][c] for c in range(3)]
+            s2 = d[0] ** 2 + d[1] ** 2 + d[2] ** 2 + e2
+            s = mp.sqrt(s2)
+            f = M[j] / (s2 * s)
+            ax = [ax[c] + f * d[c] for c in range(3)]
+            ph -= M[j] / s
+            qq = max(qq, (w[0] ** 2 + w[1] ** 2 + w[2] ** 2) / s2, f)
+            scale += M[j] / s2
+        for c in range(3):
+            assert abs(a[i, c] - float(ax[c])) <= 1e-14 * float(scale)
+        assert abs(phi[i] - float(ph)) <= 1e-14 * abs(float(ph))
+        assert abs(q[i] - float(qq)) <= 1e-14 * float(qq)
