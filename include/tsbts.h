@@ -51,8 +51,10 @@ typedef struct {
                         energy. */
   int n_iter;        /* passes per era (Alg. 2 "iteration limit"); 1 = plain
                         block steps; default 3 */
-  int era_mode;      /* 0 = fixed era (Sec. 3), 1 = dynamic era (Alg. 3);
-                        default 0 */
+  int era_mode;      /* 0 = fixed era (Sec. 3), 1 = dynamic era (Alg. 3:
+                        last minus first next block time, clamped to
+                        [dt_max 2^-dyn_min_log2, dt_max], rounded up to a
+                        power of two); default 0 */
   int era_log2;      /* fixed era = 2^-era_log2 time units, 0..k_max;
                         default 3 */
   int dyn_min_log2;  /* dynamic era lower limit = dt_max * 2^-dyn_min_log2;

@@ -260,7 +260,10 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
 
 long long era_ticks(tsbts_ctx* c) {
   if (c->cfg.era_mode == 0) return 1LL << (c->cfg.k_max - c->cfg.era_log2);
-  // Alg. 3: last block time - first block time, clamped, power of two
+  // Alg. 3: last block time - first block time, clamped to
+  // [dt_max 2^-dyn_min_log2, dt_max], rounded up to a power of two (the
+  // smallest era that holds that span, so the largest steps are not cut
+  // off by an era end)
   const long long lo0 = LLONG_MAX, hi0 = LLONG_MIN;
   ck(cudaMemcpyAsync(&c->d_ctl->first, &lo0, sizeof lo0,
                      cudaMemcpyHostToDevice, c->s), "era reset");
@@ -274,7 +277,7 @@ long long era_ticks(tsbts_ctx* c) {
   long long e = c->h_ctl->last - c->h_ctl->first;
   e = std::min(std::max(e, lo), c->dtmax_t);
   long long p2 = 1;
-  while (2 * p2 <= e) p2 *= 2;
+  while (p2 < e) p2 *= 2;  // dt_max is a power of two >= e
   return p2;
 }
 

@@ -105,7 +105,9 @@ def test_iteration_counts(orc, n_iter):
 
 
 def test_dynamic_era_bit_exact(orc):
-    """Alg. 3 with exclusion of long-step bodies (Sec. 4), ragged n."""
+    """Alg. 3 (eras from the device's block-time extrema and R11), ragged
+    n. Bodies excluded by an era end are covered by the fixed-era resume
+    test, where the era is shorter than the largest step."""
     m, r, v = inputs.plummer(1000, 7)
     kw = dict(eps=1 / 256, eta=0.02, dt_max=1 / 8, n_iter=3, era_mode=1,
               era_log2=3, k_max=20)

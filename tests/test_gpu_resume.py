@@ -26,7 +26,7 @@ def era_end(orc, m, r, v, t2, **kw):
     o = orc.Sim(m, r, v, log=True, k_max=K_MAX, **kw)
     o.run(t2)
     _, te = o.eras()
-    return int(te[len(te) // 2]) * 2.0 ** -K_MAX, o
+    return int(te[(len(te) - 1) // 2]) * 2.0 ** -K_MAX, o
 
 
 @pytest.mark.parametrize("precision,n,era_mode", [

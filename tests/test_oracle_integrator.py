@@ -213,13 +213,13 @@ def test_iteration_improves_reversibility_and_energy(orc):
 
 
 def test_dynamic_era_rules(orc):
-    """Alg. 3: eras are last minus first block time, clamped to
-    [dt_max / 8, dt_max] and rounded to a power of two; bodies whose next
-    time passes the era end wait for a later era (Sec. 4)."""
+    """Alg. 3: an era is last minus first block time, clamped to
+    [dt_max / 8, dt_max] and rounded up to a power of two (R11); bodies
+    whose next time passes the era end wait for a later era (Sec. 4)."""
     m, r, v = inputs.plummer(96, seed=1)
     kmax = 20
-    s = sim(orc, m, r, v, eta=0.05, era_mode=1, dt_max=1 / 8, log=True,
-            k_max=kmax)
+    kw = dict(eta=0.02, era_mode=1, dt_max=1 / 8, k_max=kmax)
+    s = sim(orc, m, r, v, log=True, **kw)
     s.run(0.5)
     assert np.isfinite(s.state()["r"]).all()
     ts, te = s.eras()
@@ -234,7 +234,21 @@ def test_dynamic_era_rules(orc):
     for e in range(len(ts)):
         sel = log["era"] == e
         assert np.all(log["tau"][sel] > ts[e]) and np.all(log["tau"][sel] <= te[e])
-    assert len(ts) > 4
+    # the rule itself, era by era, from the state at each era start
+    # (integrating to an era end reproduces the same eras)
+    probe = sim(orc, m, r, v, **kw)
+    shorter = 0
+    for k in range(len(ts) - 1):
+        probe.run(int(ts[k]) * 2.0 ** -kmax)
+        st = probe.state()
+        nxt = st["tau"] + st["dt"]
+        span = min(max(int(nxt.max() - nxt.min()), dtm // 8), dtm)
+        want = 1
+        while want < span:
+            want *= 2
+        assert L[k] == want, (k, span, L[k])
+        shorter += int(want < dtm)
+    assert len(ts) > 2 and shorter > 0
 
 
 def test_t_end_must_be_on_tick_grid(orc):

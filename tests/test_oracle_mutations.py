@@ -57,8 +57,11 @@ MUTANTS = [
      '/ s2; /* |v_ij|^2/s^2 */',
      '/ (s2 - eps2 + 1e-300); /* |v_ij|^2/s^2 */'),
     ('tsbts_oracle.c', 'dyn_no_pow2', 'Alg. 3 era not rounded to a power of two',
-     '  while (2 * p <= e) p *= 2;\n  return p;',
+     '  while (p < e) p *= 2;\n  return p;',
      '  return e;'),
+    ('tsbts_oracle.c', 'era_rounded_down', 'R11 era rounded down, not up',
+     '  while (p < e) p *= 2;',
+     '  while (2 * p <= e) p *= 2;'),
     ('tsbts_oracle.c', 'fwd_no_commensurate', 'R9 without commensurability',
      'while (tau % c != 0) c /= 2;',
      ''),
@@ -189,6 +192,7 @@ def plant(top, fname, anchor, repl):
     os.makedirs(tdir)
     for f in pin_tests() + ["conftest.py"]:
         shutil.copy(os.path.join(HERE, f), tdir)
+    shutil.copytree(os.path.join(HERE, "golden"), os.path.join(tdir, "golden"))
 
 
 def caught(top):

@@ -40,6 +40,7 @@ assert 2.0 ** -ERA_LOG2 == ERA
 def max_energy_error(seed, n_iter):
     import oracle
     from paper_1205_2288_gb300 import inputs
+    oracle.set_threads(1)  # one process per run
     m, r, v = inputs.plummer(PAPER["n_bodies"], 1000 + seed)
     s = oracle.Sim(m, r, v, eps=PAPER["eps_plummer"], eta=PAPER["eta"],
                    dt_max=PAPER["dt_max"], n_iter=n_iter, era_mode=0,
