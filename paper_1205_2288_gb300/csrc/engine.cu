@@ -261,9 +261,9 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
 long long era_ticks(tsbts_ctx* c) {
   if (c->cfg.era_mode == 0) return 1LL << (c->cfg.k_max - c->cfg.era_log2);
   // Alg. 3: last block time - first block time, clamped to
-  // [dt_max 2^-dyn_min_log2, dt_max], rounded up to a power of two (the
-  // smallest era that holds that span, so the largest steps are not cut
-  // off by an era end)
+  // [dt_max 2^-dyn_min_log2, dt_max], then the smallest power of two at
+  // least that long (R11: rounding down would leave most eras shorter than
+  // the largest steps in use)
   const long long lo0 = LLONG_MAX, hi0 = LLONG_MIN;
   ck(cudaMemcpyAsync(&c->d_ctl->first, &lo0, sizeof lo0,
                      cudaMemcpyHostToDevice, c->s), "era reset");
