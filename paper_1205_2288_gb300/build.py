@@ -36,6 +36,7 @@ def sources():
 
 def _deps():
     return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(CSRC, "*.h")) +
             glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
 
 

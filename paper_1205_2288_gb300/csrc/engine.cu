@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "era_rule.h"
 
 using namespace tsbts;
 
@@ -260,10 +261,7 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
 
 long long era_ticks(tsbts_ctx* c) {
   if (c->cfg.era_mode == 0) return 1LL << (c->cfg.k_max - c->cfg.era_log2);
-  // Alg. 3: last block time - first block time, clamped to
-  // [dt_max 2^-dyn_min_log2, dt_max], then the smallest power of two at
-  // least that long (R11: rounding down would leave most eras shorter than
-  // the largest steps in use)
+  // Alg. 3 from the device's block-time extrema (era_rule.h)
   const long long lo0 = LLONG_MAX, hi0 = LLONG_MIN;
   ck(cudaMemcpyAsync(&c->d_ctl->first, &lo0, sizeof lo0,
                      cudaMemcpyHostToDevice, c->s), "era reset");
@@ -272,13 +270,8 @@ long long era_ticks(tsbts_ctx* c) {
   launch_next_time_extrema(c->B, c->d_ctl, c->s);
   c->launches += 1;
   read_ctl(c);
-  long long lo = c->dtmax_t >> c->cfg.dyn_min_log2;
-  if (lo < 1) lo = 1;
-  long long e = c->h_ctl->last - c->h_ctl->first;
-  e = std::min(std::max(e, lo), c->dtmax_t);
-  long long p2 = 1;
-  while (p2 < e) p2 *= 2;  // dt_max is a power of two >= e
-  return p2;
+  return tsbts_dynamic_era_ticks(c->h_ctl->first, c->h_ctl->last,
+                                 c->dtmax_t, c->cfg.dyn_min_log2);
 }
 
 int step_era_impl(tsbts_ctx* c, long long tau_end) {
