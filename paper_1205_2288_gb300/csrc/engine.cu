@@ -867,20 +867,12 @@ int tsbts_set_state(tsbts_ctx* ctx, double t, const double* m,
     return fail(ctx, TSBTS_ERR_ARG, "t must be a whole number of ticks >= 0");
   const long long T = (long long)tt;
   const int n = ctx->n;
-  // a state that could end an era; every step indexes the level histogram
-  for (int i = 0; i < n; ++i) {
-    const long long d = dt_ticks[i], ti = tau_ticks[i];
-    bool ok = d >= 1 && d <= ctx->dtmax_t && (d & (d - 1)) == 0 && ti >= 0 &&
-              ti % d == 0 && ti <= T && T - ti < d;
-    ok = ok && std::isfinite(m[i]) && dts[i] > 0.0;
-    for (int c = 0; c < 3; ++c)
-      ok = ok && std::isfinite(r[3 * (size_t)i + c]) &&
-           std::isfinite(v[3 * (size_t)i + c]) &&
-           std::isfinite(a[3 * (size_t)i + c]);
-    if (!ok)
-      return fail(ctx, TSBTS_ERR_ARG,
-                  "state cannot end an era at body " + std::to_string(i));
-  }
+  // a state that could end an era (era_rule.h), checked before any copy
+  const long long bad = tsbts_first_bad_body(T, ctx->dtmax_t, n, m, r, v, a,
+                                             tau_ticks, dt_ticks, dts);
+  if (bad >= 0)
+    return fail(ctx, TSBTS_ERR_ARG,
+                "state cannot end an era at body " + std::to_string(bad));
   try {
     ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
     // body-major host vectors to the per-component device arrays
