@@ -32,7 +32,7 @@ T_END = 100
 SEED0 = 2000
 
 
-def max_energy_error(seed, era_mode):
+def max_energy_error(seed, era_mode, t_end=T_END):
     import oracle
     from paper_1205_2288_gb300 import inputs
     oracle.set_threads(1)  # one process per run
@@ -43,20 +43,38 @@ def max_energy_error(seed, era_mode):
                    era_mode=era_mode, era_log2=era_log2, k_max=20)
     e0 = sum(s.energy())
     worst = 0.0
-    for t in range(1, T_END + 1):
+    for t in range(1, t_end + 1):
         s.run(float(t))
         worst = max(worst, abs(sum(s.energy()) - e0) / abs(e0))
     return worst
 
 
-def test_dynamic_era_errors_in_the_range_of_the_fixed_era():
+def ratios(t_end):
     seeds = range(PAPER["n_realisations"])
-    jobs = [(seed, mode) for seed in seeds for mode in (0, 1)]
+    jobs = [(seed, mode, t_end) for seed in seeds for mode in (0, 1)]
     with cf.ProcessPoolExecutor(max_workers=min(len(jobs), os.cpu_count()),
                                 mp_context=mp.get_context("spawn")) as ex:
         out = dict(zip(jobs, ex.map(max_energy_error, *zip(*jobs))))
-    fixed = np.array([out[(s, 0)] for s in seeds])
-    dyn = np.array([out[(s, 1)] for s in seeds])
+    fixed = np.array([out[(s, 0, t_end)] for s in seeds])
+    dyn = np.array([out[(s, 1, t_end)] for s in seeds])
+    return dyn, fixed
+
+
+def test_dynamic_era_errors_in_the_range_of_the_fixed_era():
+    dyn, fixed = ratios(T_END)
     ratio = dyn / fixed
     assert np.sum(dyn <= fixed) >= len(fixed) / 2, ratio
     assert math.exp(np.mean(np.log(ratio))) < 1.2, ratio
+
+
+@pytest.mark.skipif(os.environ.get("TSBTS_LONG") != "1",
+                    reason="long run: set TSBTS_LONG=1")
+def test_over_the_papers_full_span():
+    """The paper's 1000 time units (~40 min of CPU time, six minutes on
+    eight cores): dynamic no
+    worse than fixed for at least half of the seeds and modestly better on
+    average (measured: 7 of 10, geometric-mean ratio 0.72)."""
+    dyn, fixed = ratios(PAPER["t_end"])
+    ratio = dyn / fixed
+    assert np.sum(dyn <= fixed) >= len(fixed) / 2, ratio
+    assert math.exp(np.mean(np.log(ratio))) < 1.0, ratio
