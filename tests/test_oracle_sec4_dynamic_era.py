@@ -71,9 +71,9 @@ def test_dynamic_era_errors_in_the_range_of_the_fixed_era():
                     reason="long run: set TSBTS_LONG=1")
 def test_over_the_papers_full_span():
     """The paper's 1000 time units (~40 min of CPU time, six minutes on
-    eight cores): dynamic no
-    worse than fixed for at least half of the seeds and modestly better on
-    average (measured: 7 of 10, geometric-mean ratio 0.72)."""
+    eight cores): dynamic no worse than fixed for at least half of the
+    seeds and modestly better on average (measured: 7 of 10, geometric-mean
+    ratio 0.72)."""
     dyn, fixed = ratios(PAPER["t_end"])
     ratio = dyn / fixed
     assert np.sum(dyn <= fixed) >= len(fixed) / 2, ratio
