@@ -167,3 +167,16 @@ def test_resume_check_agrees_with_the_oracle(lib):
                 refused += 1
             checked += 1
     assert checked == 450 and 100 < refused < 450
+    # spoils that only one condition refuses
+    T = int(3 / 16 * 2 ** K_MAX)
+    st = s.state()
+    for tau, dt in ((0, 2 * dt_max_t),     # step above dt_max only
+                    (T + 4, 4),            # ahead of the system time only
+                    (T - 4, 4),            # next time not after T only
+                    (T - 2, 4),            # off its step grid only
+                    (T, 3)):               # not a power of two only
+        bad = {k: np.copy(x) for k, x in st.items()}
+        bad["tau"][5], bad["dt"][5] = tau, dt
+        assert first_bad(lib, T, dt_max_t, m, bad) == 5, (tau, dt)
+        with pytest.raises(ValueError):
+            s.set_state(3 / 16, m, bad)
