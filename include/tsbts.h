@@ -87,10 +87,12 @@ typedef struct {
   int64_t history_capacity; /* records per pass buffer */
   int64_t t_sys_ticks;    /* system time in ticks */
   double force_ms;        /* device time in the force kernel, summed over
-                             launches when timing is on, else 0 */
-  int64_t force_launches;
+                             the timed launches (tsbts_set_timing), else 0 */
+  int64_t force_launches;   /* force launches timed */
   int64_t kernel_launches;  /* kernels of this library launched by the
                                context since tsbts_init */
+  int64_t force_interactions; /* interactions (n_act * n) of the block
+                                 steps whose force launch was timed */
 } tsbts_stats;
 
 void tsbts_config_default(tsbts_config* cfg);
@@ -181,9 +183,13 @@ int tsbts_set_state(tsbts_ctx* ctx, double t, const double* m,
 
 int tsbts_get_stats(tsbts_ctx* ctx, tsbts_stats* out);
 
-/* Time every force launch with CUDA events (adds a small host cost per
- * launch); the sum appears in tsbts_stats.force_ms. */
-int tsbts_set_timing(tsbts_ctx* ctx, int enable);
+/* Time force launches with CUDA events around them; the sums appear in
+ * tsbts_stats (force_ms, force_launches, force_interactions). period = 0:
+ * off; 1: every block step; k > 1: the block steps of every k-th chunk of
+ * steps (one graph replay or stream batch), a sample that keeps the cost
+ * of the events (which also serialise the step's launches) to about 1/k.
+ * TSBTS_ERR_ARG for period < 0. */
+int tsbts_set_timing(tsbts_ctx* ctx, int period);
 
 /* Record the block schedule of the following calls: per block step the
  * era index, pass, block time and active count, and per active body its
@@ -338,6 +344,20 @@ int tsbts_adjoint_loss_grad(tsbts_ctx* ctx, const double* m, const double* r0,
                             double* g_v0, double* g_m, int device_ptrs);
 
 int tsbts_adjoint_get_stats(tsbts_ctx* ctx, tsbts_adjoint_stats* out);
+
+/* Measured throughput of one execution pipe of the current device, the
+ * denominator of the force kernels' rooflines (the pair term of Eq. 3 is
+ * bound by the FMA pipe, not by the tensor cores or memory). kind:
+ *   0 = FP32 fma (1 FMA-pipe op per lane and instruction),
+ *   1 = packed FP32 fma.f32x2 (2 ops per lane and instruction),
+ *   2 = FP64 fma, 3 = FP32 rsqrt (special-function unit).
+ * Every thread of an 8-blocks-per-SM grid runs 8 independent chains of
+ * `iters` operations (1 <= iters <= 2^30); one warm-up launch, then one
+ * launch timed with CUDA events on the legacy default stream. Writes lane
+ * operations per second to *ops_per_s and the timed launch's duration to
+ * *ms (may be NULL). Allocates 4 bytes of device memory for the call.
+ * TSBTS_ERR_ARG: bad kind, iters or null output. */
+int tsbts_pipe_peak(int kind, int64_t iters, double* ops_per_s, double* ms);
 
 /* Library version string. */
 const char* tsbts_version(void);

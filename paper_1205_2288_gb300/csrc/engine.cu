@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -61,7 +62,9 @@ void alloc_history(tsbts_ctx* c, int b, long long cap) {
 
 void release_graph(tsbts_ctx* c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gexec_t) cudaGraphExecDestroy(c->gexec_t);
   c->gexec = nullptr;
+  c->gexec_t = nullptr;
   c->graph_dirty = true;
 }
 
@@ -107,30 +110,36 @@ ForceArgs force_args_engine(tsbts_ctx* c, int p) {
   fa.eps2 = c->eps * c->eps;
   fa.eps2f = (float)(c->eps * c->eps);
   fa.exact = c->exact;
-  fa.plans = c->d_plans;
+  fa.plans = nullptr;
   return fa;
 }
 
-// work plan of the force kernel for every active count 0..n, chosen on the
-// host (device memory: 16 B per body; above 2^20 bodies the kernel chooses
-// its plan itself)
-void build_plan_table(tsbts_ctx* c) {
-  c->d_plans = nullptr;
-  if (c->n > (1 << 20)) return;
-  std::vector<Plan> t(c->n + 1);
-  for (int k = 0; k <= c->n; ++k)
-    t[k] = plan_force(c->cfg.precision, c->exact, k, c->n, c->fl.grid,
-                      c->B.part_cap);
-  c->d_plans = dalloc<Plan>(c->allocs, t.size());
-  ck(cudaMemcpyAsync(c->d_plans, t.data(), sizeof(Plan) * t.size(),
-                     cudaMemcpyHostToDevice, c->s),
-     "copy plans");
-  ck(cudaStreamSynchronize(c->s), "synchronize");
+// active counts of the plan buckets: 1, 2, 4, ... below n, then n
+std::vector<int> plan_buckets(int n) {
+  std::vector<int> b;
+  for (long long k = 1; k < n; k *= 2) b.push_back((int)k);
+  b.push_back(n);
+  return b;
 }
 
-// one block step: A (select + predict), B (force), C (correct). Timing
-// events inside a captured graph are external event nodes, so that they
-// are recorded (and timed) at every replay.
+// work plan of the force kernel per bucket of active counts, chosen on the
+// host by the cost model (the mixed path replaces them with measured plans
+// after the first force launch); passed to every launch by value
+void build_plan_table(tsbts_ctx* c) {
+  const std::vector<int> b = plan_buckets(c->n);
+  c->pt = PlanTable{};
+  c->pt.nb = (int)b.size();
+  for (size_t k = 0; k < b.size(); ++k)
+    c->pt.b[k] = plan_force(c->cfg.precision, c->exact, b[k], c->n,
+                            c->fl.grid, c->B.part_cap);
+}
+
+// one block step: A (select + predict), B (force), C (correct). Plain
+// stream order between them: launched with programmatic stream
+// serialization the next kernel's blocks start early and wait on the GPU,
+// which measured slower per block step on GB300. Timing events inside a
+// captured graph are external event nodes, so that they are recorded (and
+// timed) at every replay.
 void enqueue_step(tsbts_ctx* c, int p, int ev_slot, bool capturing) {
   const History& HA = c->H[0];
   const History& HB = c->H[1];
@@ -144,15 +153,18 @@ void enqueue_step(tsbts_ctx* c, int p, int ev_slot, bool capturing) {
     ck(cudaGetLastError(), "ensemble step launch");
     return;
   }
-  launch_select_predict(c->B, c->P, HA, HB, p, c->s);
+  ck(launch_select_predict(c->B, c->P, HA, HB, p, false, c->s),
+     "select/predict launch");
   if (ev_slot >= 0)
     ck(cudaEventRecordWithFlags(c->ev[2 * ev_slot], c->s, evflags), "event");
-  ck(launch_force(c->cfg.precision, force_args_engine(c, p), c->fl, c->s),
+  ck(launch_force(c->cfg.precision, force_args_engine(c, p), c->fl, c->s,
+                  &c->pt, false),
      "force launch");
   if (ev_slot >= 0)
     ck(cudaEventRecordWithFlags(c->ev[2 * ev_slot + 1], c->s, evflags),
        "event");
-  launch_correct(c->B, c->P, HA, HB, p, c->correct_grid, c->s);
+  ck(launch_correct(c->B, c->P, HA, HB, p, c->correct_grid, false, c->s),
+     "correct launch");
 }
 
 void ensure_events(tsbts_ctx* c, int steps) {
@@ -163,28 +175,35 @@ void ensure_events(tsbts_ctx* c, int steps) {
   }
 }
 
-void build_graph(tsbts_ctx* c) {
-  release_graph(c);
+// the graph of graph_steps block steps, with (timed) or without event
+// nodes around each force launch
+void build_graph(tsbts_ctx* c, bool timed) {
+  cudaGraphExec_t& ex = timed ? c->gexec_t : c->gexec;
   const int G = c->cfg.graph_steps;
-  if (c->timing) ensure_events(c, G);
+  if (timed) ensure_events(c, G);
   cudaGraph_t g;
   ck(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal),
      "begin capture");
   try {
-    for (int k = 0; k < G; ++k)
-      enqueue_step(c, k & 1, c->timing ? k : -1, true);
+    for (int k = 0; k < G; ++k) enqueue_step(c, k & 1, timed ? k : -1, true);
   } catch (...) {
     cudaStreamEndCapture(c->s, &g);
     throw;
   }
   ck(cudaStreamEndCapture(c->s, &g), "end capture");
-  cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
   ck(e, "graph instantiate");
-  c->graph_dirty = false;
 }
 
-void accumulate_timing(tsbts_ctx* c, int real_steps) {
+// whether the next chunk of block steps carries timing events: every
+// timing-th chunk (the sample that tsbts_stats reports)
+bool timed_chunk(tsbts_ctx* c) {
+  return c->timing > 0 && (c->chunk_no++ % c->timing) == 0;
+}
+
+void accumulate_timing(tsbts_ctx* c, int real_steps,
+                       unsigned long long inter) {
   for (int k = 0; k < real_steps; ++k) {
     float ms = 0;
     ck(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]),
@@ -192,6 +211,7 @@ void accumulate_timing(tsbts_ctx* c, int real_steps) {
     c->force_ms += ms;
     c->force_launches += 1;
   }
+  c->force_inter += (long long)inter;
 }
 
 struct NoProgress {};
@@ -221,15 +241,23 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
   const int G = c->cfg.graph_steps;
   unsigned long long steps0 = c->h_ctl->steps;
   long long pass_steps = 0;
+  unsigned long long inter0 = c->h_ctl->inter;
   if (G > 0) {
-    if (c->graph_dirty || !c->gexec) build_graph(c);
+    if (c->graph_dirty) {
+      release_graph(c);
+      c->graph_dirty = false;
+    }
     for (;;) {
-      ck(cudaGraphLaunch(c->gexec, c->s), "graph launch");
+      const bool timed = timed_chunk(c);
+      cudaGraphExec_t& ex = timed ? c->gexec_t : c->gexec;
+      if (!ex) build_graph(c, timed);
+      ck(cudaGraphLaunch(ex, c->s), "graph launch");
       c->launches += (long long)per_step * G;
       read_ctl(c);
       const int real = (int)(c->h_ctl->steps - steps0);
       steps0 = c->h_ctl->steps;
-      if (c->timing) accumulate_timing(c, real);
+      if (timed) accumulate_timing(c, real, c->h_ctl->inter - inter0);
+      inter0 = c->h_ctl->inter;
       if (c->h_ctl->done || c->h_ctl->err) break;
       check_progress(c, real, pass_steps += real, tau_e);
     }
@@ -238,16 +266,18 @@ int run_pass(tsbts_ctx* c, int pass, long long tau_e, long long est_steps) {
                                                   est_steps / 2 + 1, 256));
     int p = 0;
     for (;;) {
-      if (c->timing) ensure_events(c, (int)chunk);
+      const bool timed = timed_chunk(c);
+      if (timed) ensure_events(c, (int)chunk);
       for (long long k = 0; k < chunk; ++k) {
-        enqueue_step(c, p, c->timing ? (int)k : -1, false);
+        enqueue_step(c, p, timed ? (int)k : -1, false);
         c->launches += per_step;
         p ^= 1;
       }
       read_ctl(c);
       const int real = (int)(c->h_ctl->steps - steps0);
       steps0 = c->h_ctl->steps;
-      if (c->timing) accumulate_timing(c, real);
+      if (timed) accumulate_timing(c, real, c->h_ctl->inter - inter0);
+      inter0 = c->h_ctl->inter;
       if (c->h_ctl->done || c->h_ctl->err) break;
       check_progress(c, real, pass_steps += real, tau_e);
       chunk = std::min<long long>(chunk * 2, 256);
@@ -286,6 +316,7 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
     const long long saved_passes = c->passes;
     const double saved_force_ms = c->force_ms;
     const long long saved_force_n = c->force_launches;
+    const long long saved_force_inter = c->force_inter;
     for (;;) {
       bool grow = false;
       long long est = 0;
@@ -343,6 +374,7 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
       c->passes = saved_passes;
       c->force_ms = saved_force_ms;
       c->force_launches = saved_force_n;
+      c->force_inter = saved_force_inter;
       launch_copy_state(c->B, c->snap, c->s);
       c->launches += 1;
       c->restarts += 1;
@@ -359,6 +391,7 @@ void setup_bodies(tsbts_ctx* c, int n) {
   B.n = n;
   auto& L = c->allocs;
   B.m = dalloc<double>(L, n);
+  B.mf = dalloc<float>(L, n);
   for (int d = 0; d < 3; ++d) {
     B.r[d] = dalloc<double>(L, n);
     B.v[d] = dalloc<double>(L, n);
@@ -502,18 +535,20 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     c->eras = c->passes = c->restarts = c->max_rec = 0;
     c->force_ms = 0;
     c->force_launches = 0;
+    c->force_inter = 0;
+    c->chunk_no = 0;
     c->launches = 0;
     c->exact = c->cfg.precision == TSBTS_FP64 &&
                (c->cfg.exact_order == 1 ||
                 (c->cfg.exact_order < 0 && n <= 8192));
     c->fl = force_launch_shape(c->cfg.precision, c->cfg.device);
-    // 32-thread blocks spread the FP64 work of small active sets over SMs
+    // one warp per block spreads the FP64 correction over the SMs
     c->correct_grid = std::max(1, std::min(c->sms * 32, (c->n + 31) / 32));
     c->ensemble = false;
     c->nc = 0;
     setup_bodies(c, (int)n);
     if (ens) {
-      c->d_plans = nullptr;
+      c->pt = PlanTable{};
       setup_ensemble(c, *ens);
     } else {
       build_plan_table(c);
@@ -558,6 +593,9 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
       fa.n_act_ptr = nullptr;
       fa.nsplit_out = c->d_nsplit;
       fa.done = nullptr;
+      fa.plan = plan_force(c->cfg.precision, c->exact, c->n, c->n,
+                           c->fl.grid, c->B.part_cap);
+      fa.has_plan = 1;
       ck(launch_force(c->cfg.precision, fa, c->fl, c->s), "init force");
       launch_init_finalize(c->B, P, c->d_nsplit, c->s);
       ck(cudaGetLastError(), "init kernels");
@@ -567,7 +605,8 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     free_list(tmp);
     if (c->h_ctl->err & kErrNonFinite)
       return fail(c, TSBTS_ERR_NONFINITE, "non-finite input or initial force");
-    if (c->cfg.precision == TSBTS_MIXED && c->d_plans && !c->ensemble) {
+    if (c->cfg.precision == TSBTS_MIXED && !c->ensemble &&
+        c->n <= (1 << 20)) {
       // measured work plans on this device for this n (first context only;
       // later contexts reuse the cached table)
       std::vector<Plan> t;
@@ -575,10 +614,8 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
       ck(autotune_mixed_plans(c->cfg.device, base, c->fl, c->d_nsplit, c->s,
                               &t),
          "force plan autotuning");
-      ck(cudaMemcpyAsync(c->d_plans, t.data(), sizeof(Plan) * t.size(),
-                         cudaMemcpyHostToDevice, c->s),
-         "copy plans");
-      ck(cudaStreamSynchronize(c->s), "synchronize");
+      const std::vector<int> b = plan_buckets(c->n);
+      for (size_t k = 0; k < b.size(); ++k) c->pt.b[k] = t[b[k]];
     }
     c->inited = true;
     c->graph_dirty = true;
@@ -897,6 +934,9 @@ int tsbts_set_state(tsbts_ctx* ctx, double t, const double* m,
     put(ctx->B.tau, tau_ticks, sizeof(long long) * n);
     put(ctx->B.dt, dt_ticks, sizeof(long long) * n);
     put(ctx->B.dts, dts, nd);
+    launch_masses_to_float(ctx->B, ctx->s);
+    ctx->launches += 1;
+    ck(cudaGetLastError(), "float masses");
     // the host buffers are read before the call returns
     ck(cudaStreamSynchronize(ctx->s), "synchronize");
     ctx->t_sys = T;
@@ -926,17 +966,17 @@ int tsbts_get_stats(tsbts_ctx* ctx, tsbts_stats* out) {
   out->t_sys_ticks = ctx->t_sys;
   out->force_ms = ctx->force_ms;
   out->force_launches = ctx->force_launches;
+  out->force_interactions = ctx->force_inter;
   out->kernel_launches = ctx->launches;
   return TSBTS_OK;
 }
 
-int tsbts_set_timing(tsbts_ctx* ctx, int enable) {
+int tsbts_set_timing(tsbts_ctx* ctx, int period) {
   int rc = check_ready(ctx);
   if (rc) return rc;
-  if (ctx->timing != (enable != 0)) {
-    ctx->timing = enable != 0;
-    ctx->graph_dirty = true;
-  }
+  if (period < 0)
+    return fail(ctx, TSBTS_ERR_ARG, "timing period must be >= 0");
+  ctx->timing = period;
   return TSBTS_OK;
 }
 
@@ -1121,6 +1161,11 @@ int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
         fa.plan = (*tp)[n_act];
     }
     fa.has_plan = 1;
+    if (std::getenv("TSBTS_PRINT_PLANS"))
+      std::fprintf(stderr, "tsbts_force n=%d n_act=%lld: ig %d n_g %d S %d "
+                   "chunk %d %s\n", ni, (long long)n_act, fa.plan.ig,
+                   fa.plan.n_g, fa.plan.S, fa.plan.chunk,
+                   fa.plan.direct ? "direct" : "tiled");
     ck(launch_force(precision, fa, fl, s), "force");
     ck(launch_force_finalize(S.part, S.nsplit, (int)n_act, a, phi, q, s),
        "force finalize");

@@ -52,14 +52,16 @@ struct tsbts_ctx {
   double* d_w = nullptr;
   double* d_eout = nullptr;
   int* d_nsplit = nullptr;  // scratch for init's split count
-  Plan* d_plans = nullptr;  // force work plan per active count
+  PlanTable pt{};            // force work plan per bucket of active counts
   ForceLaunch fl{};
   int correct_grid = 1;
   // counters
   long long eras = 0, passes = 0, restarts = 0;
   long long max_rec = 0;
   // timing
-  bool timing = false;
+  int timing = 0;            // time every timing-th chunk of steps (0: off)
+  long long chunk_no = 0;    // chunks of block steps launched since init
+  long long force_inter = 0; // interactions of the timed steps
   std::vector<cudaEvent_t> ev;
   double force_ms = 0;
   long long force_launches = 0;
@@ -68,7 +70,8 @@ struct tsbts_ctx {
   long long lg_cap = 0;
   std::vector<void*> lg_allocs;
   // CUDA graph of graph_steps block steps
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec = nullptr;    // without timing events
+  cudaGraphExec_t gexec_t = nullptr;  // with events around each force
   bool graph_dirty = true;
   // ensemble of independent clusters (tsbts_init_ensemble)
   bool ensemble = false;

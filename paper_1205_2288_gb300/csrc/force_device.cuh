@@ -15,6 +15,8 @@ constexpr int kTileMix = 256;   // j per shared-memory tile, mixed
 constexpr int kLaneMinMix = 16; // fewest j per thread in a split item
 constexpr int kLaneMinF64 = 8;
 constexpr int kSplitCap = 16;   // most j-splits of one active body
+constexpr int kSplitCapDirect = 128;  // most j-splits of a direct-load plan
+constexpr int kDirectBatch = 4;  // j records per lane loaded in one batch
 
 // tuning of the mixed pair loop (compile-time; defaults measured on GB300)
 #ifndef TSBTS_MIX_UNROLL
@@ -560,12 +562,28 @@ __device__ void mixed_direct_item(const ForceArgs& A, int n_act, const Plan& P,
     float ax = 0, ay = 0, az = 0, ph = 0;
     const int j0 = split * P.chunk;
     const int j1 = min(A.n, j0 + P.chunk);
+    // kDirectBatch j records per lane are loaded in one batch before any is
+    // used, so a small item waits for one round trip to L2, not one per j
     int cnt = 0;
-#pragma unroll 4
-    for (int j = j0 + jl; j < j1; j += JG) {
-      const float4 h = A.jhi[j], l = A.jlo[j], vv = A.jv[j];
-      if (j != i) pair_mixed_g(I, h, l, vv, eps2, ax, ay, az, ph, q);
-      if (++cnt == kTileMix) {
+    for (int jb = j0 + jl; jb < j1; jb += JG * kDirectBatch) {
+      float4 h[kDirectBatch], l[kDirectBatch], vv[kDirectBatch];
+#pragma unroll
+      for (int u = 0; u < kDirectBatch; ++u) {
+        const int j = jb + u * JG;
+        if (j < j1) {
+          h[u] = __ldg(A.jhi + j);
+          l[u] = __ldg(A.jlo + j);
+          vv[u] = __ldg(A.jv + j);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kDirectBatch; ++u) {
+        const int j = jb + u * JG;
+        if (j < j1 && j != i)
+          pair_mixed_g(I, h[u], l[u], vv[u], eps2, ax, ay, az, ph, q);
+      }
+      cnt += kDirectBatch;
+      if (cnt >= kTileMix) {
         cnt = 0;
         ds_add(sx, ax);
         ds_add(sy, ay);

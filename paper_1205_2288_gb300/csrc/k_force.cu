@@ -19,12 +19,15 @@
 // j records are staged tile by tile in shared memory with coalesced loads
 // and read back as broadcasts; the pair loop is FMA-pipe bound.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <iterator>
 #include <map>
 #include <mutex>
 #include <vector>
 
 #include "force_device.cuh"
+#include "step_device.cuh"
 
 namespace tsbts {
 
@@ -102,14 +105,55 @@ __device__ __forceinline__ Plan make_plan(int n_act, int n, int grid,
   return p;
 }
 
-__global__ void __launch_bounds__(kThreads) force_fp64_kernel(ForceArgs A) {
-  if (A.done && *A.done) return;
-  const int n_act = A.n_act_fixed >= 0 ? A.n_act_fixed : *A.n_act_ptr;
-  if (n_act <= 0) return;
-  const Plan P = A.has_plan ? A.plan
-                 : A.plans  ? A.plans[n_act]
-                            : make_plan(n_act, A.n, gridDim.x, A.exact,
-                                        A.part_cap, kLaneMinF64, kTileF64);
+// The plan of a launch: fixed by the caller, from the bucket table, from a
+// per-count table, or chosen on the device.
+__device__ __forceinline__ Plan launch_plan(const ForceArgs& A,
+                                            const PlanTable& PT, int n_act,
+                                            int lane_min, int precision) {
+  if (A.has_plan) return A.plan;
+  if (PT.nb > 0) {
+    Plan p = PT.b[plan_bucket(n_act, PT.nb)];
+    p.n_g = (n_act + p.ig - 1) / p.ig;
+    if (precision) {
+      // a bucket's plan was measured at the bucket's largest count; a
+      // smaller count has fewer i-groups, so more j-splits keep the grid
+      // full (within the per-lane work floor and the partial buffer)
+      const int jg = kThreads / p.ig;
+      const int cap = p.direct ? kSplitCapDirect : 2 * kSplitCap;
+      const int lane_min = p.direct ? 2 : kLaneMinMix;
+      int S = min((int)gridDim.x / p.n_g, cap);
+      S = min(S, max(1, A.n / (jg * lane_min)));
+      while (S > p.S && (long long)S * 5 * n_act > A.part_cap) --S;
+      if (S > p.S) {
+        p.S = S;
+        p.chunk = (((A.n + S - 1) / S) + 1) & ~1;
+      }
+    }
+    return p;
+  }
+  if (A.plans) return A.plans[n_act];
+  return make_plan(n_act, A.n, gridDim.x, precision ? 0 : A.exact,
+                   A.part_cap, lane_min, precision ? kTileMix : kTileF64);
+}
+
+// Launch prologue shared by both precisions: wait for the prediction
+// kernel (programmatic dependent launch), read the active count. Returns
+// false when there is nothing to do.
+__device__ __forceinline__ bool force_prologue(const ForceArgs& A,
+                                               int& n_act) {
+  pdl_wait();
+  pdl_launch_dependents();
+  if (A.done && *A.done) return false;
+  n_act = A.n_act_fixed >= 0 ? A.n_act_fixed : *A.n_act_ptr;
+  return n_act > 0;
+}
+
+__global__ void __launch_bounds__(kThreads)
+    force_fp64_kernel(const __grid_constant__ ForceArgs A,
+                      const __grid_constant__ PlanTable PT) {
+  int n_act = 0;
+  if (!force_prologue(A, n_act)) return;
+  const Plan P = launch_plan(A, PT, n_act, kLaneMinF64, 0);
   if (blockIdx.x == 0 && threadIdx.x == 0 && A.nsplit_out)
     *A.nsplit_out = P.S;
   __shared__ F64Tile T;
@@ -127,22 +171,18 @@ __global__ void __launch_bounds__(kThreads) force_fp64_kernel(ForceArgs A) {
 }
 
 __global__ void __launch_bounds__(kThreads, kMixMinBlocks)
-    force_mixed_kernel(ForceArgs A) {
-  if (A.done && *A.done) return;
-  const int n_act = A.n_act_fixed >= 0 ? A.n_act_fixed : *A.n_act_ptr;
-  if (n_act <= 0) return;
-  const Plan P = A.has_plan ? A.plan
-                 : A.plans  ? A.plans[n_act]
-                            : make_plan(n_act, A.n, gridDim.x, 0, A.part_cap,
-                                        kLaneMinMix, kTileMix);
+    force_mixed_kernel(const __grid_constant__ ForceArgs A,
+                       const __grid_constant__ PlanTable PT) {
+  int n_act = 0;
+  if (!force_prologue(A, n_act)) return;
+  const Plan P = launch_plan(A, PT, n_act, kLaneMinMix, 1);
   if (blockIdx.x == 0 && threadIdx.x == 0 && A.nsplit_out)
     *A.nsplit_out = P.S;
   __shared__ MixTile T;
   __shared__ float red[9][kThreads];
-  if (P.direct) {
+  if (P.direct && P.ig <= 32) {
+    // direct loads serve the narrow groups
     switch (P.ig) {
-      case 128: mixed_items_direct<128>(A, n_act, P, red); break;
-      case 64: mixed_items_direct<64>(A, n_act, P, red); break;
       case 32: mixed_items_direct<32>(A, n_act, P, red); break;
       case 16: mixed_items_direct<16>(A, n_act, P, red); break;
       case 8: mixed_items_direct<8>(A, n_act, P, red); break;
@@ -242,12 +282,22 @@ ForceLaunch force_launch_shape(int precision, int device) {
 }
 
 cudaError_t launch_force(int precision, const ForceArgs& fa,
-                         const ForceLaunch& fl, cudaStream_t s) {
+                         const ForceLaunch& fl, cudaStream_t s,
+                         const PlanTable* pt, bool pdl) {
+  const PlanTable none{};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(fl.grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
   if (precision)
-    force_mixed_kernel<<<fl.grid, kThreads, 0, s>>>(fa);
-  else
-    force_fp64_kernel<<<fl.grid, kThreads, 0, s>>>(fa);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, force_mixed_kernel, fa, pt ? *pt : none);
+  return cudaLaunchKernelEx(&cfg, force_fp64_kernel, fa, pt ? *pt : none);
 }
 
 // ---------------------------------------------------------------------
@@ -271,34 +321,40 @@ std::map<TuneKey, std::vector<Plan>> g_tuned;
 // the wider groups and direct loads for the narrower ones, split counts
 // {1, 2, 3, 4, 6, 8, 12, 16} within the per-thread work floor and the
 // partial-sum buffer, plus for each width the split count with the best
-// wave fill of the grid
+// wave fill of the grid. Direct-load plans also try up to kSplitCapDirect
+// splits of a few j per lane: a small active set then spreads over the
+// whole grid and each lane waits for one batch of loads.
 std::vector<Plan> candidates(int b, int n, int grid, long long part_cap) {
   static const int kS[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  static const int kSDirect[] = {24, 32, 48, 64, 96, 128};
   std::vector<Plan> out;
   for (int ig = kThreads; ig >= 1; ig >>= 1) {
     if (ig > 2 * b && ig > 1) continue;
     const int jg = kThreads / ig;
     const int n_g = (b + ig - 1) / ig;
-    long long smax = n / ((long long)jg * kLaneMinMix);
-    smax = std::max<long long>(1, std::min<long long>(smax, kSplitCap));
-    std::vector<int> ss(std::begin(kS), std::end(kS));
-    int best_s = 1;
-    double best_fill = 0;
-    for (int S = 1; S <= smax; ++S) {
-      const long long items = (long long)n_g * S;
-      const double fill =
-          (double)items / (double)(((items + grid - 1) / grid) * grid);
-      if (fill > best_fill + 1e-9) {
-        best_fill = fill;
-        best_s = S;
-      }
-    }
-    ss.push_back(best_s);
-    std::sort(ss.begin(), ss.end());
-    ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
     for (int direct = 0; direct <= 1; ++direct) {
       if (direct && ig > 32) continue;
       if (!direct && ig < 8) continue;
+      const int lane_min = direct ? 2 : kLaneMinMix;
+      const int cap = direct ? kSplitCapDirect : kSplitCap;
+      long long smax = n / ((long long)jg * lane_min);
+      smax = std::max<long long>(1, std::min<long long>(smax, cap));
+      std::vector<int> ss(std::begin(kS), std::end(kS));
+      if (direct) ss.insert(ss.end(), std::begin(kSDirect), std::end(kSDirect));
+      int best_s = 1;
+      double best_fill = 0;
+      for (int S = 1; S <= smax; ++S) {
+        const long long items = (long long)n_g * S;
+        const double fill =
+            (double)items / (double)(((items + grid - 1) / grid) * grid);
+        if (fill > best_fill + 1e-9) {
+          best_fill = fill;
+          best_s = S;
+        }
+      }
+      ss.push_back(best_s);
+      std::sort(ss.begin(), ss.end());
+      ss.erase(std::unique(ss.begin(), ss.end()), ss.end());
       for (int S : ss) {
         if (S > smax) continue;
         if ((long long)S * 5 * b > part_cap) continue;
@@ -334,15 +390,20 @@ cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
   std::vector<int> buckets;
   for (long long b = 1; b < n; b *= 2) buckets.push_back((int)b);
   buckets.push_back(n);
-  cudaEvent_t e0, e1;
-  cudaError_t err = cudaEventCreate(&e0);
-  if (err != cudaSuccess) return err;
-  err = cudaEventCreate(&e1);
-  if (err != cudaSuccess) {
-    cudaEventDestroy(e0);
-    return err;
-  }
+  // each candidate: one warm-up launch, then kReps batches of kBatch
+  // back-to-back launches, each batch bracketed by events (the event clock
+  // ticks in microseconds, coarser than a small launch); its time is the
+  // median batch over kBatch (robust to a stray slow batch)
+  constexpr int kReps = 3;
+  constexpr int kBatch = 8;
+  cudaEvent_t ev[kReps + 1];
+  cudaError_t err = cudaSuccess;
+  int made = 0;
+  for (; made <= kReps && err == cudaSuccess; ++made)
+    err = cudaEventCreate(&ev[made]);
+  if (err != cudaSuccess) made -= 1;
   std::vector<Plan> best(buckets.size());
+  std::vector<float> best_t(buckets.size(), 0.f);
   for (size_t bi = 0; bi < buckets.size() && err == cudaSuccess; ++bi) {
     const int b = buckets[bi];
     float best_ms = 1e30f;
@@ -356,24 +417,34 @@ cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
       fa.plan = p;
       fa.has_plan = 1;
       launch_force(1, fa, fl, s);
-      cudaEventRecord(e0, s);
-      const int reps = 3;
-      for (int r = 0; r < reps; ++r) launch_force(1, fa, fl, s);
-      cudaEventRecord(e1, s);
-      err = cudaEventSynchronize(e1);
+      for (int r = 0; r < kReps; ++r) {
+        cudaEventRecord(ev[r], s);
+        for (int q = 0; q < kBatch; ++q) launch_force(1, fa, fl, s);
+      }
+      cudaEventRecord(ev[kReps], s);
+      err = cudaEventSynchronize(ev[kReps]);
       if (err != cudaSuccess) break;
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
+      float t[kReps];
+      for (int r = 0; r < kReps; ++r) cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+      std::sort(t, t + kReps);
+      const float ms = t[kReps / 2] / kBatch;
       if (ms < best_ms) {
         best_ms = ms;
         best[bi] = p;
       }
     }
+    best_t[bi] = best_ms;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
   if (err == cudaSuccess) err = cudaGetLastError();
   if (err != cudaSuccess) return err;
+  if (std::getenv("TSBTS_PRINT_PLANS")) {
+    for (size_t bi = 0; bi < buckets.size(); ++bi)
+      std::fprintf(stderr,
+                   "tsbts plan n=%d n_act<=%d: ig %d S %d chunk %d %s %.2f us\n",
+                   n, buckets[bi], best[bi].ig, best[bi].S, best[bi].chunk,
+                   best[bi].direct ? "direct" : "tiled", 1e3 * best_t[bi]);
+  }
   table->assign(n + 1, Plan{kThreads, 0, 1, n, 0});
   size_t bi = 0;
   for (int k = 1; k <= n; ++k) {

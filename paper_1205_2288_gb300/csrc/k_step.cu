@@ -1,7 +1,10 @@
 // Block-step kernels of the TSBTS library (Sec. 2 Alg. 2 steps 3-8, Sec. 4
 // Alg. 3): era/pass set-up, block selection fused with the prediction or
 // time-symmetric interpolation of every body, correction (Eq. 1) with the
-// next-step choice (Eq. 4, Alg. 1) and the era-history append, energy.
+// next-step choice (Eq. 4, Alg. 1) and the era-history append, the history
+// reorder between passes, energy. Each kernel of a block step waits
+// (griddepcontrol.wait) before reading what its predecessor wrote, so the
+// launches may also use programmatic stream serialization.
 //
 // The loop is device-resident: every kernel reads the block time, active
 // count and pass state from the control block, so a whole chunk of block
@@ -11,7 +14,7 @@
 // Block selection uses the commensurability of block steps: each body sits
 // on a multiple of its own power-of-two step, so the next block time is the
 // next multiple of the smallest populated step after the current block
-// time, and a per-level body count (updated by the correction kernel)
+// time, and a per-level body count (updated by the correction)
 // replaces the paper's sort by block time.
 #include "step_device.cuh"
 #include "tsbts_kernels.cuh"
@@ -77,16 +80,21 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
   __shared__ long long s_tn;
   __shared__ int s_stop;
   Ctl* ctl = P.ctl;
-  // this body's inputs, loaded before the block time is known
-  const int pass = ctl->pass;
+  // everything below reads what the previous step's force launch wrote
+  pdl_wait();
+  pdl_launch_dependents();
+  // this body's inputs, loaded before the block time and the pass are
+  // known (the segment cache too: it is not used in the first pass), so
+  // that every load of the kernel is in flight at once
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   long long tj = 0, dtj = 0;
   PredIn L;
   if (j < B.n) {
     tj = B.tau[j];
     dtj = B.dt[j];
-    load_pred_in(B, j, pass > 0, L);
+    load_pred_in(B, j, true, L);
   }
+  const int pass = ctl->pass;
   if (threadIdx.x < 32) {
     // smallest populated step = highest populated level, one warp-wide load
     const int lane = threadIdx.x;
@@ -140,40 +148,137 @@ __global__ void select_predict_kernel(Bodies B, Params P, History HA,
 // ---------------------------------------------------------------------
 // Step C: correction (Eq. 1), next step (pass 0: standard block step;
 // passes >= 1: Alg. 1 with Eq. 4), history append, level counts.
+//
+// The force launch leaves S split partial sums per active body (S = 1 for
+// FP64 sums in ascending j). With few splits one thread takes a body and
+// adds its partials in split order. With many splits (a small active set
+// spread over the whole grid) a warp takes a body: lane l adds the
+// contiguous splits [l per, (l + 1) per) in order, a fixed shuffle tree
+// combines the lanes, and lane 0 corrects the body; the partials then
+// arrive in one round of loads instead of S. Every order is fixed, so the
+// result does not depend on timing.
 // ---------------------------------------------------------------------
+constexpr int kWarpSumMinSplits = 9;  // S at or above this: a warp per body
+
+// one body's correction after its force sums are known; level-count
+// changes go to the block's dh
+__device__ __forceinline__ void correct_one(const Bodies& B, const Params& P,
+                                            const History& cur,
+                                            const History& prev,
+                                            const StepSlot& sl, int pass,
+                                            int k, const double an[3],
+                                            double q, int* dh) {
+  Ctl* ctl = P.ctl;
+  const int i = B.act[k];
+  const Corrected cr = correct_body(B, P, cur, prev, i, an, q, sl.tau_next,
+                                    pass, sl.nrec + k, &ctl->err);
+  const long long c = cr.d_new;
+  if (cr.underflow) atomicAdd(&ctl->underflow, 1ULL);
+  if (c != cr.d_old) {
+    atomicSub(&dh[level_of(cr.d_old, P.k_max)], 1);
+    atomicAdd(&dh[level_of(c, P.k_max)], 1);
+  }
+  if (P.lg_cap > 0) {
+    const long long e = sl.lg_base + k;
+    if (e < P.lg_cap) {
+      P.lg_i[e] = i;
+      P.lg_dt[e] = c;
+    }
+  }
+}
+
 __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
                                int p) {
+  // everything below reads what the force launch wrote
+  pdl_wait();
+  pdl_launch_dependents();
   Ctl* ctl = P.ctl;
-  if (ctl->done) return;
+  // the step's values and the pass-over flag in one round of loads
+  const int done = ctl->done;
+  const StepSlot sl = ctl->slot[p];
+  const int pass = ctl->pass;
+  if (done) return;
   __shared__ int dh[kMaxLevels];
   for (int t = threadIdx.x; t < kMaxLevels; t += blockDim.x) dh[t] = 0;
   __syncthreads();
-  const StepSlot sl = ctl->slot[p];
   const int n_act = sl.cnt;
-  const long long tn = sl.tau_next;
   const int S = sl.nsplit;
-  const int pass = ctl->pass;
   const History& cur = HA;
   const History& prev = HB;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act;
-       k += gridDim.x * blockDim.x) {
-    const int i = B.act[k];
-    double an[3], q;
-    sum_partials(B.part, n_act, S, k, an, q);
-    const Corrected cr = correct_body(B, P, cur, prev, i, an, q, tn, pass,
-                                      sl.nrec + k, &ctl->err);
-    const long long c = cr.d_new;
-    if (cr.underflow) atomicAdd(&ctl->underflow, 1ULL);
-    if (c != cr.d_old) {
-      atomicSub(&dh[level_of(cr.d_old, P.k_max)], 1);
-      atomicAdd(&dh[level_of(c, P.k_max)], 1);
-    }
-    if (P.lg_cap > 0) {
-      const long long e = sl.lg_base + k;
-      if (e < P.lg_cap) {
-        P.lg_i[e] = i;
-        P.lg_dt[e] = c;
+  const double* part = B.part;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  // a warp per body only while every body gets its own warp: the FP64
+  // correction of one lane costs a whole warp's issue slots
+  if (S >= kWarpSumMinSplits && n_act <= nw) {
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int per = (S + 31) >> 5;
+    for (int k = w0; k < n_act; k += nw) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, q = 0.0;
+      int have = 0;
+      const int lo = lane * per, hi = min(S, lo + per);
+      for (int b0 = lo; b0 < hi; b0 += 4) {
+        double x[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (b0 + u < hi) {
+            const double* pp = part + (long long)(b0 + u) * 5 * n_act;
+            x[u][0] = pp[k];
+            x[u][1] = pp[n_act + k];
+            x[u][2] = pp[2LL * n_act + k];
+            x[u][3] = pp[4LL * n_act + k];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (b0 + u < hi) {
+            if (!have) {
+              s0 = x[u][0];
+              s1 = x[u][1];
+              s2 = x[u][2];
+              q = x[u][3];
+              have = 1;
+            } else {
+              s0 = __dadd_rn(s0, x[u][0]);
+              s1 = __dadd_rn(s1, x[u][1]);
+              s2 = __dadd_rn(s2, x[u][2]);
+              q = fmax(q, x[u][3]);
+            }
+          }
+        }
       }
+      for (int off = 16; off >= 1; off >>= 1) {
+        const double o0 = __shfl_down_sync(kFull, s0, off);
+        const double o1 = __shfl_down_sync(kFull, s1, off);
+        const double o2 = __shfl_down_sync(kFull, s2, off);
+        const double oq = __shfl_down_sync(kFull, q, off);
+        const int oh = __shfl_down_sync(kFull, have, off);
+        if (lane < off && oh) {
+          if (have) {
+            s0 = __dadd_rn(s0, o0);
+            s1 = __dadd_rn(s1, o1);
+            s2 = __dadd_rn(s2, o2);
+            q = fmax(q, oq);
+          } else {
+            s0 = o0;
+            s1 = o1;
+            s2 = o2;
+            q = oq;
+            have = 1;
+          }
+        }
+      }
+      if (lane == 0) {
+        const double an[3] = {s0, s1, s2};
+        correct_one(B, P, cur, prev, sl, pass, k, an, q, dh);
+      }
+    }
+  } else {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_act;
+         k += gridDim.x * blockDim.x) {
+      double an[3], q;
+      sum_partials(part, n_act, S, k, an, q);
+      correct_one(B, P, cur, prev, sl, pass, k, an, q, dh);
     }
   }
   // level-count changes of this block, one global atomic per changed level
@@ -182,7 +287,7 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
     if (dh[t]) atomicAdd(&ctl->hist[t], dh[t]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     StepSlot& nx = ctl->slot[p ^ 1];
-    nx.tau_c = tn;
+    nx.tau_c = sl.tau_next;
     nx.tau_next = 0;
     nx.nrec = sl.nrec + n_act;
     nx.lg_base = sl.lg_base + n_act;
@@ -195,7 +300,7 @@ __global__ void correct_kernel(Bodies B, Params P, History HA, History HB,
       if (s < P.lg_cap) {
         P.lg_era[s] = ctl->era;
         P.lg_pass[s] = pass;
-        P.lg_tau[s] = tn;
+        P.lg_tau[s] = sl.tau_next;
         P.lg_nact[s] = n_act;
       }
       ctl->log_steps = s + 1;
@@ -345,6 +450,7 @@ __global__ void load_aos_kernel(Bodies B, const double* m, const double* r,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n;
        i += gridDim.x * blockDim.x) {
     B.m[i] = m[i];
+    B.mf[i] = (float)m[i];
     bool ok = isfinite(m[i]);
     for (int c = 0; c < 3; ++c) {
       const double x = r[3LL * i + c], u = v[3LL * i + c];
@@ -359,6 +465,13 @@ __global__ void load_aos_kernel(Bodies B, const double* m, const double* r,
     B.act[i] = i;
     if (!ok) atomicOr(&ctl->err, kErrNonFinite);
   }
+}
+
+// float masses of the mixed j records from the FP64 masses
+__global__ void masses_to_float_kernel(Bodies B) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B.n;
+       i += gridDim.x * blockDim.x)
+    B.mf[i] = (float)B.m[i];
 }
 
 // j data of the initial state (prediction to t = 0 is the state itself)
@@ -505,16 +618,37 @@ void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
   pass_setup_kernel<<<grid_for(B.n, 256, 2048), 256, 0, s>>>(B, P, cur);
 }
 
-void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
-                           const History& HB, int p, cudaStream_t s) {
+cudaError_t launch_select_predict(const Bodies& B, const Params& P,
+                                  const History& HA, const History& HB, int p,
+                                  bool pdl, cudaStream_t s) {
   // 64-thread blocks spread the FP64 prediction over more SMs
-  select_predict_kernel<<<grid_for(B.n, 64, 1 << 30), 64, 0, s>>>(B, P, HA,
-                                                                  HB, p);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_for(B.n, 64, 1 << 30));
+  cfg.blockDim = dim3(64);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, select_predict_kernel, B, P, HA, HB, p);
 }
 
-void launch_correct(const Bodies& B, const Params& P, const History& HA,
-                    const History& HB, int p, int grid, cudaStream_t s) {
-  correct_kernel<<<grid, 32, 0, s>>>(B, P, HA, HB, p);
+cudaError_t launch_correct(const Bodies& B, const Params& P,
+                           const History& HA, const History& HB, int p,
+                           int grid, bool pdl, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, correct_kernel, B, P, HA, HB, p);
 }
 
 void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s) {
@@ -528,6 +662,10 @@ void launch_next_time_extrema(const Bodies& B, Ctl* ctl, cudaStream_t s) {
 void launch_load_aos(const Bodies& B, const double* m, const double* r,
                      const double* v, Ctl* ctl, cudaStream_t s) {
   load_aos_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B, m, r, v, ctl);
+}
+
+void launch_masses_to_float(const Bodies& B, cudaStream_t s) {
+  masses_to_float_kernel<<<grid_for(B.n, 256), 256, 0, s>>>(B);
 }
 
 void launch_init_jdata(const Bodies& B, const Params& P, cudaStream_t s) {

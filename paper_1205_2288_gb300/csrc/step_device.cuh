@@ -11,6 +11,44 @@
 
 namespace tsbts {
 
+// Double-single split with integer operations only (the FP64 pipe of this
+// GPU is 64 times narrower than the FP32 one, and a conversion costs as
+// much as an FP64 add): hi is x with its significand cut to the leading 24
+// bits, lo the exact remainder rounded to float, so hi + lo equals x to
+// about 2^-48 relative. Doubles outside 2^-70 .. 2^100 in magnitude (and
+// zeros, non-finite values) take the conversion path.
+__device__ __forceinline__ void split_ds(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 1023 - 70 || e > 1023 + 100) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+    return;
+  }
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned long long m = b & ((1ULL << 52) - 1);
+  hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) |
+                       (unsigned)(m >> 29));
+  const unsigned r = (unsigned)(m & ((1u << 29) - 1));
+  const float scale = __uint_as_float((unsigned)(e - 1023 - 52 + 127) << 23);
+  lo = __uint_as_float(__float_as_uint(__uint2float_rn(r) * scale) | sign);
+}
+
+// x rounded to float (to nearest, ties away) with integer operations; same
+// range rule as split_ds
+__device__ __forceinline__ float to_float(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 1023 - 70 || e > 1023 + 100) return __double2float_rn(x);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned long long m = b & ((1ULL << 52) - 1);
+  // exponent and significand as one integer: the rounding carry may
+  // propagate into the exponent, which is the correct result
+  const unsigned mag = ((unsigned)(e - 1023 + 127) << 23) +
+                       (unsigned)((m + (1ULL << 28)) >> 29);
+  return __uint_as_float(sign | mag);
+}
+
 // j data of the force kernels at the block time: FP64 arrays or the packed
 // double-single records of the mixed path
 __device__ __forceinline__ void store_prediction(const Bodies& B,
@@ -23,12 +61,12 @@ __device__ __forceinline__ void store_prediction(const Bodies& B,
       B.pv[c][j] = vp[c];
     }
   } else {
-    const float xh = (float)rp[0], yh = (float)rp[1], zh = (float)rp[2];
-    B.jhi[j] = make_float4(xh, yh, zh, (float)B.m[j]);
-    B.jlo[j] = make_float4((float)(rp[0] - (double)xh),
-                           (float)(rp[1] - (double)yh),
-                           (float)(rp[2] - (double)zh), 0.f);
-    B.jv[j] = make_float4((float)vp[0], (float)vp[1], (float)vp[2], 0.f);
+    float h[3], l[3];
+    for (int c = 0; c < 3; ++c) split_ds(rp[c], h[c], l[c]);
+    B.jhi[j] = make_float4(h[0], h[1], h[2], B.mf[j]);
+    B.jlo[j] = make_float4(l[0], l[1], l[2], 0.f);
+    B.jv[j] = make_float4(to_float(vp[0]), to_float(vp[1]), to_float(vp[2]),
+                          0.f);
   }
 }
 
@@ -125,11 +163,24 @@ __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
       have = true;
     } else if (ta < tn && tb > tn) {
       const HermiteW w = hermite_weights(ta, tb, tn, P.inv_ticks);
-      for (int d = 0; d < 3; ++d) {
-        rp[d] = hermite1(w, L.seg[d + 0], L.seg[d + 3], L.seg[d + 9],
-                         L.seg[d + 12]);
-        vp[d] = hermite1(w, L.seg[d + 3], L.seg[d + 6], L.seg[d + 12],
-                         L.seg[d + 15]);
+      if (P.precision == 0) {
+        for (int d = 0; d < 3; ++d) {
+          rp[d] = hermite1(w, L.seg[d + 0], L.seg[d + 3], L.seg[d + 9],
+                           L.seg[d + 12]);
+          vp[d] = hermite1(w, L.seg[d + 3], L.seg[d + 6], L.seg[d + 12],
+                           L.seg[d + 15]);
+        }
+      } else {
+        // mixed path: the same cubic with fused multiply-adds (the FP32
+        // force reads only the double-single rounding of it)
+        for (int d = 0; d < 3; ++d) {
+          rp[d] = fma(w.h00, L.seg[d + 0],
+                      fma(w.h10h, L.seg[d + 3],
+                          fma(w.h01, L.seg[d + 9], w.h11h * L.seg[d + 12])));
+          vp[d] = fma(w.h00, L.seg[d + 3],
+                      fma(w.h10h, L.seg[d + 6],
+                          fma(w.h01, L.seg[d + 12], w.h11h * L.seg[d + 15])));
+        }
       }
       have = true;
     }
@@ -137,7 +188,16 @@ __device__ __forceinline__ void predict_body(const Bodies& B, const Params& P,
   if (!have) {
     if (!L.have_state) load_pred_state(B, j, L);
     const double h = __dmul_rn((double)(tn - tj), P.inv_ticks);
-    for (int d = 0; d < 3; ++d) taylor1(L.r[d], L.v[d], L.a[d], h, rp[d], vp[d]);
+    if (P.precision == 0) {
+      for (int d = 0; d < 3; ++d)
+        taylor1(L.r[d], L.v[d], L.a[d], h, rp[d], vp[d]);
+    } else {
+      // mixed path: Eq. 2 in Horner form with fused multiply-adds
+      for (int d = 0; d < 3; ++d) {
+        rp[d] = fma(fma(0.5 * L.a[d], h, L.v[d]), h, L.r[d]);
+        vp[d] = fma(L.a[d], h, L.v[d]);
+      }
+    }
   }
   store_prediction(B, P, j, rp, vp);
 }
@@ -160,6 +220,21 @@ __device__ __forceinline__ void sum_partials(const double* part, int n_act,
     an[2] = __dadd_rn(an[2], pp[2 * n_act + k]);
     q = fmax(q, pp[4 * n_act + k]);
   }
+}
+
+// The step estimate of Eq. 3, eta / sqrt(q). FP64 path: correctly rounded
+// square root and division, as the plain definition. Mixed path (q is a
+// maximum of FP32 pair terms): the FP32 reciprocal square root refined by
+// one Newton-Raphson step for 1/sqrt(q) in FP64, about 2^-40 relative,
+// with a third of the dependent FP64 latency; q outside 1e-30 .. 1e30 (and
+// 0, inf, NaN) takes the FP64 form.
+__device__ __forceinline__ double step_estimate(const Params& P, double q) {
+  if (P.precision != 0 && q > 1e-30 && q < 1e30) {
+    const double y0 = (double)rsqrtf((float)q);
+    const double y1 = y0 * fma(-0.5 * q * y0, y0, 1.5);
+    return P.eta * y1;
+  }
+  return __ddiv_rn(P.eta, __dsqrt_rn(q));
 }
 
 struct Corrected {
@@ -267,14 +342,24 @@ __device__ __forceinline__ Corrected correct_body(const Bodies& B,
   // Eq. 1
   const double h = __dmul_rn((double)d, P.inv_ticks);
   double rn[3], vn[3];
-  for (int c = 0; c < 3; ++c) {
-    double rp, vp;
-    taylor1(r0[c], v0[c], a0[c], h, rp, vp);
-    rn[c] = rp;
-    vn[c] = __dadd_rn(v0[c],
-                      __dmul_rn(__dmul_rn(0.5, __dadd_rn(a0[c], an[c])), h));
+  if (P.precision == 0) {
+    for (int c = 0; c < 3; ++c) {
+      double rp, vp;
+      taylor1(r0[c], v0[c], a0[c], h, rp, vp);
+      rn[c] = rp;
+      vn[c] = __dadd_rn(
+          v0[c], __dmul_rn(__dmul_rn(0.5, __dadd_rn(a0[c], an[c])), h));
+    }
+  } else {
+    // mixed path: the same update with fused multiply-adds (half the
+    // dependent FP64 operations; the forces carry FP32 pair terms)
+    const double hh = 0.5 * h;
+    for (int c = 0; c < 3; ++c) {
+      rn[c] = fma(fma(hh, a0[c], v0[c]), h, r0[c]);
+      vn[c] = fma(a0[c] + an[c], hh, v0[c]);
+    }
   }
-  const double dts = __ddiv_rn(P.eta, __dsqrt_rn(q));
+  const double dts = step_estimate(P, q);
   Corrected out;
   out.d_old = d;
   out.underflow = 0;

@@ -74,6 +74,7 @@ struct Ctl {
 struct Bodies {
   int n;
   double* m;
+  float* mf;         // masses rounded to float (the mixed j records)
   double* r[3];
   double* v[3];
   double* a[3];
@@ -190,6 +191,33 @@ struct ForceArgs {
   int exact;           // FP64: no j-split
 };
 
+// Measured work plans of the integrator's force launch, one per power-of-two
+// bucket of active counts (bucket b holds counts in (2^(b-1), 2^b], the last
+// bucket ends at n); passed by value so that choosing the plan costs no
+// memory access once the active count is known.
+constexpr int kMaxBuckets = 26;
+struct PlanTable {
+  Plan b[kMaxBuckets];
+  int nb;
+};
+
+__host__ __device__ inline int plan_bucket(int n_act, int nb) {
+  int b = 0;
+  while (b + 1 < nb && (1 << b) < n_act) ++b;
+  return b;
+}
+
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialization attribute may start while its predecessor in
+// the stream still runs; it must wait before reading what the predecessor
+// writes. Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------
 // FP64 step arithmetic, op by op.
 // ---------------------------------------------------------------------
@@ -274,9 +302,23 @@ struct HermiteW {
   double h00, h10h, h01, h11h;
 };
 
+// t / D in FP64 for whole numbers of ticks t and D > 0. Record times of one
+// body differ by its power-of-two steps, so D is almost always a power of
+// two; then the quotient is an exact scaling by 2^-log2(D), which equals the
+// correctly rounded division bit for bit and costs one multiply instead of
+// the FP64 division sequence.
+__device__ inline double ticks_ratio(long long t, long long D) {
+  if ((D & (D - 1)) == 0) {
+    const int e = 63 - __clzll(D);
+    const double inv = __longlong_as_double((long long)(1023 - e) << 52);
+    return __dmul_rn((double)t, inv);
+  }
+  return __ddiv_rn((double)t, (double)D);
+}
+
 __device__ inline HermiteW hermite_weights(long long ta, long long tb,
                                            long long t, double inv_ticks) {
-  const double x = __ddiv_rn((double)(t - ta), (double)(tb - ta));
+  const double x = ticks_ratio(t - ta, tb - ta);
   const double h = __dmul_rn((double)(tb - ta), inv_ticks);
   const double omx = __dsub_rn(1.0, x);
   HermiteW w;
@@ -309,8 +351,7 @@ __device__ inline double history_dts_at(const History& H, int start, int end,
   while (c + 1 < end && H.tau[c + 1] <= t) ++c;
   if (H.tau[c] == t) return H.dts[c];
   if (c + 1 >= end) return fallback;
-  const double w = __ddiv_rn((double)(t - H.tau[c]),
-                             (double)(H.tau[c + 1] - H.tau[c]));
+  const double w = ticks_ratio(t - H.tau[c], H.tau[c + 1] - H.tau[c]);
   return __dadd_rn(H.dts[c], __dmul_rn(__dsub_rn(H.dts[c + 1], H.dts[c]), w));
 }
 
@@ -335,8 +376,11 @@ const std::vector<Plan>* tuned_plans(int device, int n, int grid);
 cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
                                  const ForceLaunch& fl, int* d_nsplit,
                                  cudaStream_t s, std::vector<Plan>* table);
+// pt (nullable): plans per bucket of active counts; pdl: launch with
+// programmatic stream serialization
 cudaError_t launch_force(int precision, const ForceArgs& fa,
-                         const ForceLaunch& fl, cudaStream_t s);
+                         const ForceLaunch& fl, cudaStream_t s,
+                         const PlanTable* pt = nullptr, bool pdl = false);
 // sum nsplit partials per active body into AoS a, phi, q
 cudaError_t launch_force_finalize(const double* part, const int* nsplit,
                                   int n_act, double* a, double* phi,

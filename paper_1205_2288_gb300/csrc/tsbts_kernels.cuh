@@ -11,10 +11,13 @@ void launch_pass_begin(Ctl* ctl, long long tau_s, long long tau_e, int pass,
                        int era, int n, cudaStream_t s);
 void launch_pass_setup(const Bodies& B, const Params& P, const History& cur,
                        cudaStream_t s);
-void launch_select_predict(const Bodies& B, const Params& P, const History& HA,
-                           const History& HB, int p, cudaStream_t s);
-void launch_correct(const Bodies& B, const Params& P, const History& HA,
-                    const History& HB, int p, int grid, cudaStream_t s);
+// pdl: launch with programmatic stream serialization
+cudaError_t launch_select_predict(const Bodies& B, const Params& P,
+                                  const History& HA, const History& HB, int p,
+                                  bool pdl, cudaStream_t s);
+cudaError_t launch_correct(const Bodies& B, const Params& P,
+                           const History& HA, const History& HB, int p,
+                           int grid, bool pdl, cudaStream_t s);
 void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s);
 // the running pass's appended records -> previous-pass records in CSR order
 void launch_history_to_csr(const Bodies& B, const History& append,
@@ -24,6 +27,8 @@ void launch_next_time_extrema(const Bodies& B, Ctl* ctl, cudaStream_t s);
 void launch_load_aos(const Bodies& B, const double* m, const double* r,
                      const double* v, Ctl* ctl, cudaStream_t s);
 void launch_init_jdata(const Bodies& B, const Params& P, cudaStream_t s);
+// B.mf from B.m (after the masses change)
+void launch_masses_to_float(const Bodies& B, cudaStream_t s);
 void launch_init_finalize(const Bodies& B, const Params& P, const int* nsplit,
                           cudaStream_t s);
 void launch_energy(const Bodies& B, const Params& P, long long T, double* w,

@@ -44,6 +44,7 @@ EXPORTS = (
     "tsbts_init_ensemble", "tsbts_ensemble_energy", "tsbts_adjoint_init",
     "tsbts_adjoint_forward", "tsbts_adjoint_vjp", "tsbts_adjoint_loss_grad",
     "tsbts_adjoint_get_stats", "tsbts_step_estimates", "tsbts_set_state",
+    "tsbts_pipe_peak",
 )
 
 
@@ -60,7 +61,8 @@ class tsbts_stats(C.Structure):
                 ("passes", I64), ("dt_underflow", I64),
                 ("era_restarts", I64), ("history_capacity", I64),
                 ("t_sys_ticks", I64), ("force_ms", C.c_double),
-                ("force_launches", I64), ("kernel_launches", I64)]
+                ("force_launches", I64), ("kernel_launches", I64),
+                ("force_interactions", I64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -138,6 +140,7 @@ def lib():
                                               C.c_int]
         L.tsbts_adjoint_get_stats.argtypes = [VP,
                                               C.POINTER(tsbts_adjoint_stats)]
+        L.tsbts_pipe_peak.argtypes = [C.c_int, I64, DP, DP]
         L.tsbts_version.argtypes = []
         L.tsbts_version.restype = C.c_char_p
         _lib = L
@@ -255,8 +258,9 @@ def tsbts_get_stats(ctx) -> dict:
     return s.as_dict()
 
 
-def tsbts_set_timing(ctx, enable: bool):
-    _check(lib().tsbts_set_timing(ctx, 1 if enable else 0), ctx)
+def tsbts_set_timing(ctx, period):
+    """0/False: off; 1/True: every block step; k > 1: every k-th chunk."""
+    _check(lib().tsbts_set_timing(ctx, int(period)), ctx)
 
 
 def tsbts_schedule_log(ctx, capacity: int):
@@ -318,6 +322,14 @@ def tsbts_force_static(precision, m, r, v, eps, idx, a, phi, q,
                                     v.data_ptr(), float(eps), idx.shape[0],
                                     idx.data_ptr(), a.data_ptr(),
                                     phi.data_ptr(), q.data_ptr(), stream))
+
+
+def tsbts_pipe_peak(kind: int, iters: int):
+    """(lane operations per second, ms) of one pipe (see tsbts.h)."""
+    ops, ms = C.c_double(), C.c_double()
+    _check(lib().tsbts_pipe_peak(int(kind), int(iters), C.byref(ops),
+                                 C.byref(ms)))
+    return ops.value, ms.value
 
 
 def tsbts_version() -> str:
@@ -490,8 +502,8 @@ class Simulation:
     def stats(self):
         return tsbts_get_stats(self.ctx)
 
-    def set_timing(self, enable=True):
-        tsbts_set_timing(self.ctx, enable)
+    def set_timing(self, period=1):
+        tsbts_set_timing(self.ctx, period)
 
     def schedule_log(self, capacity):
         tsbts_schedule_log(self.ctx, capacity)

@@ -241,10 +241,23 @@ def test_force_timing_counts_real_steps(orc, graph_steps):
     o = orc.Sim(m, r, v, **kw)
     o.run(0.25)
     g = tsbts.Simulation(m, r, v, graph_steps=graph_steps, **kw)
-    g.set_timing(True)
+    g.set_timing(1)
     g.step_era(0.25)
     st = g.stats()
     assert st["force_launches"] == st["block_steps"] == o.stats()["block_steps"]
+    assert st["force_interactions"] == st["interactions"]
     assert st["force_ms"] > 0
     assert st["kernel_launches"] >= 3 * st["block_steps"]
     assert_same_state(o, g)
+    g.close()
+    # a sample: every third chunk of steps is timed, the rest run without
+    # events; the results stay the same
+    g = tsbts.Simulation(m, r, v, graph_steps=graph_steps, **kw)
+    g.set_timing(3)
+    g.step_era(0.25)
+    st = g.stats()
+    assert 0 < st["force_launches"] < st["block_steps"]
+    assert 0 < st["force_interactions"] < st["interactions"]
+    assert st["force_ms"] > 0
+    assert_same_state(o, g)
+    g.close()
