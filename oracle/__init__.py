@@ -36,7 +36,8 @@ class OrcCfg(C.Structure):
                 ("era_log2", C.c_int), ("k_max", C.c_int),
                 ("dyn_min_log2", C.c_int), ("log", C.c_int),
                 ("eps", C.c_double), ("eta", C.c_double),
-                ("dt_max", C.c_double), ("conv_tol", C.c_double)]
+                ("dt_max", C.c_double), ("conv_tol", C.c_double),
+                ("trace_body", C.c_int64)]
 
 
 def build(force: bool = False) -> str:
@@ -92,6 +93,9 @@ def lib():
             L.orc_era_log.argtypes = [C.c_void_p, I64P, I64P]
             L.orc_era_log.restype = I64
             L.orc_destroy.argtypes = [C.c_void_p]
+            L.orc_trace_get.argtypes = [C.c_void_p, I32P, I32P, I64P, I32P,
+                                        DP]
+            L.orc_trace_get.restype = I64
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             L.orc_hist_find.argtypes = [I64, I64P, I64]
@@ -335,12 +339,13 @@ class Sim:
 
     def __init__(self, m, r, v, *, eps, eta, dt_max, n_iter=3, era_mode=0,
                  era_log2=3, k_max=20, dyn_min_log2=3, log=False,
-                 conv_tol=0.0):
+                 conv_tol=0.0, trace_body=-1):
         self.m, r, v = _d(m), _d(r), _d(v)
         self.n = self.m.shape[0]
         self.k_max = k_max
         cfg = OrcCfg(n_iter, era_mode, era_log2, k_max, dyn_min_log2,
-                     1 if log else 0, eps, eta, dt_max, conv_tol)
+                     1 if log else 0, eps, eta, dt_max, conv_tol,
+                     int(trace_body))
         self._s = lib().orc_create(self.n, _p(self.m), _p(r), _p(v),
                                    C.byref(cfg))
 
@@ -402,6 +407,19 @@ class Sim:
         L.orc_log_get(self._s, _p(era, I32P), _p(pas, I32P), _p(tau, I64P),
                       _p(nact, I32P), _p(ei, I32P), _p(edt, I64P))
         return dict(era=era, pass_=pas, tau=tau, n_act=nact, idx=ei, dt=edt)
+
+    def trace(self):
+        """The traced body's entries (see orc_trace_get): dict of era,
+        pass_, tau, kind (0 predicted, 1 corrected) and r, v, a (k, 3)."""
+        L = lib()
+        k = L.orc_trace_get(self._s, None, None, None, None, None)
+        era, pas = np.zeros(k, np.int32), np.zeros(k, np.int32)
+        tau, kind = np.zeros(k, np.int64), np.zeros(k, np.int32)
+        rva = np.zeros((k, 9))
+        L.orc_trace_get(self._s, _p(era, I32P), _p(pas, I32P), _p(tau, I64P),
+                        _p(kind, I32P), _p(rva))
+        return dict(era=era, pass_=pas, tau=tau, kind=kind, r=rva[:, 0:3],
+                    v=rva[:, 3:6], a=rva[:, 6:9])
 
     def eras(self):
         L = lib()

@@ -271,12 +271,52 @@ struct orc_sim {
   int64_t *lg_tau, *lg_dt;
   int64_t lg_steps, lg_steps_cap, lg_ent, lg_ent_cap;
   int64_t *era_s, *era_e, n_era_log, era_cap;
+  /* trace of one body (cfg.trace_body) */
+  int32_t *tr_era, *tr_pass, *tr_kind;
+  int64_t* tr_tau;
+  double* tr_rva;
+  int64_t tr_n, tr_cap;
 };
 
 static void* xmalloc(size_t bytes) {
   void* p = malloc(bytes ? bytes : 1);
   if (!p) abort();
   return p;
+}
+
+static void trace_push(orc_sim* s, int era, int pass, int64_t tau, int kind,
+                       const double* r, const double* v, const double* a) {
+  if (s->tr_n == s->tr_cap) {
+    s->tr_cap = s->tr_cap ? 2 * s->tr_cap : 1024;
+    s->tr_era = realloc(s->tr_era, sizeof(int32_t) * (size_t)s->tr_cap);
+    s->tr_pass = realloc(s->tr_pass, sizeof(int32_t) * (size_t)s->tr_cap);
+    s->tr_kind = realloc(s->tr_kind, sizeof(int32_t) * (size_t)s->tr_cap);
+    s->tr_tau = realloc(s->tr_tau, sizeof(int64_t) * (size_t)s->tr_cap);
+    s->tr_rva = realloc(s->tr_rva, sizeof(double) * 9 * (size_t)s->tr_cap);
+    if (!s->tr_era || !s->tr_pass || !s->tr_kind || !s->tr_tau || !s->tr_rva)
+      abort();
+  }
+  const int64_t k = s->tr_n++;
+  s->tr_era[k] = era;
+  s->tr_pass[k] = pass;
+  s->tr_tau[k] = tau;
+  s->tr_kind[k] = kind;
+  for (int c = 0; c < 3; ++c) {
+    s->tr_rva[9 * k + c] = r[c];
+    s->tr_rva[9 * k + 3 + c] = v[c];
+    s->tr_rva[9 * k + 6 + c] = a ? a[c] : 0.0;
+  }
+}
+
+int64_t orc_trace_get(orc_sim* s, int32_t* era, int32_t* pass, int64_t* tau,
+                      int32_t* kind, double* rva) {
+  const size_t k = (size_t)s->tr_n;
+  if (era) memcpy(era, s->tr_era, sizeof(int32_t) * k);
+  if (pass) memcpy(pass, s->tr_pass, sizeof(int32_t) * k);
+  if (tau) memcpy(tau, s->tr_tau, sizeof(int64_t) * k);
+  if (kind) memcpy(kind, s->tr_kind, sizeof(int32_t) * k);
+  if (rva) memcpy(rva, s->tr_rva, sizeof(double) * 9 * k);
+  return s->tr_n;
 }
 
 static void log_step(orc_sim* s, int era, int pass, int64_t tau, int nact) {
@@ -477,6 +517,9 @@ static void run_pass(orc_sim* s, int era_idx, int pass, int64_t tau_e) {
                s->vp + 3 * j);
       }
     }
+    const int64_t tb = s->cfg.trace_body;
+    if (tb >= 0 && tb < n && !s->is_act[tb])
+      trace_push(s, era_idx, pass, tn, 0, s->rp + 3 * tb, s->vp + 3 * tb, NULL);
     /* Alg. 2 step 5: forces on the active bodies */
     orc_forces(n, s->m, s->rp, s->vp, s->cfg.eps, na, s->act, s->an, s->phin,
                s->qn);
@@ -513,6 +556,9 @@ static void run_pass(orc_sim* s, int era_idx, int pass, int64_t tau_e) {
       }
       uf += u;
     }
+    if (tb >= 0 && tb < n && s->is_act[tb])
+      trace_push(s, era_idx, pass, tn, 1, s->r + 3 * tb, s->v + 3 * tb,
+                 s->a + 3 * tb);
     s->stats[4] += uf;
     s->stats[0] += 1;
     s->stats[1] += na * n;
@@ -700,6 +746,8 @@ void orc_destroy(orc_sim* s) {
   free(s->act); free(s->is_act);
   free(s->lg_era); free(s->lg_pass); free(s->lg_nact); free(s->lg_i);
   free(s->lg_tau); free(s->lg_dt);
+  free(s->tr_era); free(s->tr_pass); free(s->tr_kind); free(s->tr_tau);
+  free(s->tr_rva);
   free(s);
 }
 

@@ -84,6 +84,8 @@ typedef struct {
                         era-end position differs from the previous pass's
                         by less than conv_tol; n_iter is then the upper
                         bound. 0: always n_iter passes. */
+  int64_t trace_body; /* >= 0: record this body's state at every block step
+                        of every pass (orc_trace_get); -1: off */
 } orc_cfg;
 
 typedef struct orc_sim orc_sim;
@@ -119,6 +121,14 @@ void orc_log_get(orc_sim* s, int32_t* step_era, int32_t* step_pass,
 /* era bounds [tau_s, tau_e] in ticks, in order; returns the era count
  * (pass NULL pointers to query the count) */
 int64_t orc_era_log(orc_sim* s, int64_t* tau_s, int64_t* tau_e);
+/* The traced body (cfg.trace_body), one entry per block step of every
+ * pass: era index, pass, block time (ticks), kind and the state rva = r, v,
+ * a (9 doubles). kind 0: the body is not active and (r, v) is the
+ * prediction the step's forces used (a unused); kind 1: the body is
+ * active and (r, v, a) is its corrected state (Eq. 1). Returns the entry
+ * count (pass NULL pointers to query it). */
+int64_t orc_trace_get(orc_sim* s, int32_t* era, int32_t* pass, int64_t* tau,
+                      int32_t* kind, double* rva);
 void orc_destroy(orc_sim* s);
 void orc_set_threads(int n);
 int orc_get_threads(void);

@@ -195,11 +195,12 @@ def plant(top, fname, anchor, repl):
     shutil.copytree(os.path.join(HERE, "golden"), os.path.join(tdir, "golden"))
 
 
-def caught(top):
+def caught(top, only=None):
     env = dict(os.environ, OMP_NUM_THREADS="2")
+    target = os.path.join("tests", only) if only else "tests"
     r = subprocess.run(
         [sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-         "tests"], cwd=top, capture_output=True, text=True, env=env,
+         target], cwd=top, capture_output=True, text=True, env=env,
         timeout=900)
     summary = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else ""
     return r.returncode == 1 and " failed" in summary and "error" not in \
@@ -216,5 +217,31 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
                                ) as ex:
         results = list(ex.map(caught, tops))
     missed = [(m[1], m[2], s) for m, (ok, s) in zip(MUTANTS, results)
+              if not ok]
+    assert not missed, missed
+
+
+# The time-symmetric interpolation of passes >= 1 (R6) was first caught
+# only by the multi-pass adjoint replay, a second restatement of the same
+# passes. The interpolation pin (test_oracle_interpolation.py) checks the
+# passes against the mathematics of the Hermite interpolant; on its own it
+# must catch every planted R6 mistake that changes a prediction.
+R6_MUTANTS = ("no_interp", "interp_same_record", "bracket_off_by_one",
+              "hermite_h11_sign", "taylor_outside_uses_record")
+
+
+def test_interpolation_pin_alone_catches_the_r6_mistakes(tmp_path):
+    chosen = [m for m in MUTANTS if m[1] in R6_MUTANTS]
+    assert len(chosen) == len(R6_MUTANTS)
+    tops = []
+    for fname, name, _, anchor, repl in chosen:
+        top = str(tmp_path / name)
+        plant(top, fname, anchor, repl)
+        tops.append(top)
+    with cf.ThreadPoolExecutor(max_workers=max(1, (os.cpu_count() or 2) // 2)
+                               ) as ex:
+        results = list(ex.map(lambda t: caught(
+            t, "test_oracle_interpolation.py"), tops))
+    missed = [(m[1], m[2], s) for m, (ok, s) in zip(chosen, results)
               if not ok]
     assert not missed, missed
