@@ -71,6 +71,17 @@ typedef struct {
                         stream owned by the context; default NULL */
   int graph_steps;   /* block steps per captured CUDA graph launch; 0 = plain
                         stream launches; default 32 */
+  double conv_tol;   /* converged iteration (0 = off, the paper's fixed
+                        pass count): after pass p >= 1 an era stops early
+                        when pass p took the same block steps as pass p - 1
+                        (every body's record times equal) and every body's
+                        position at the end of the pass is within conv_tol
+                        of pass p - 1's; n_iter still bounds the passes.
+                        Single systems only; default 0 */
+  int64_t max_pass_steps; /* watchdog: a pass that takes more block steps
+                        than this stops with TSBTS_ERR_TIMEOUT (0 = the
+                        bound no working step loop can exceed: one step per
+                        tick of the era); default 0 */
 } tsbts_config;
 
 typedef struct tsbts_ctx tsbts_ctx;
@@ -142,8 +153,8 @@ int tsbts_ensemble_energy(tsbts_ctx* ctx, double* ekin, double* epot);
  * receives the new system time. Bodies whose step overshoots an era end
  * wait for a later era (Sec. 4), so body times may lag the system time.
  * TSBTS_ERR_NONFINITE: a force or step estimate became non-finite;
- * TSBTS_ERR_TIMEOUT: a pass stopped advancing the block time (both
- * poison the context). */
+ * TSBTS_ERR_TIMEOUT: a pass stopped advancing the block time or took more
+ * block steps than config.max_pass_steps (both poison the context). */
 int tsbts_step_era(tsbts_ctx* ctx, double t_end, double* t_reached);
 
 /* Kinetic, softened potential and total energy at the system time (the
@@ -239,9 +250,12 @@ int tsbts_release_scratch(void);
  * not call cudaMalloc or cudaFree because those calls can synchronise the
  * device. The paper has no counterpart; this is a property of the library.
  *
- * Same arguments, results and tolerances as tsbts_force (the FP64 path with
- * ascending-j sums gives identical results; other paths may round
- * differently because the work plan is chosen without measurement). It
+ * Same arguments, results and tolerances as tsbts_force: DEVICE pointers
+ * m[n], r[n*3], v[n*3], idx[n_act] (int32, each value in [0, n); the
+ * library does not check them), a[n_act*3], phi[n_act], q[n_act] (the FP64
+ * path with ascending-j sums gives identical results; other paths may
+ * round differently because the work plan is chosen without
+ * measurement). It
  * allocates nothing and calls no allocating routine: its scratch (packed j
  * records and j-split partial sums) is a fixed array of about 9 MB inside
  * the library that every GPU loading the library holds until the process

@@ -68,12 +68,19 @@ void release_graph(tsbts_ctx* c) {
   c->graph_dirty = true;
 }
 
-void release_all(tsbts_ctx* c) {
+// keep_history: the era-history buffers survive (a re-initialisation with
+// the same body count reuses what earlier eras grew them to, so the first
+// era of the new run does not overflow and re-run again)
+void release_all(tsbts_ctx* c, bool keep_history = false) {
   release_graph(c);
   if (c->s) cudaStreamSynchronize(c->s);
   free_list(c->allocs);
-  free_list(c->hist_allocs[0]);
-  free_list(c->hist_allocs[1]);
+  if (!keep_history) {
+    free_list(c->hist_allocs[0]);
+    free_list(c->hist_allocs[1]);
+    c->H[0] = History{};
+    c->H[1] = History{};
+  }
   free_list(c->lg_allocs);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   c->ev.clear();
@@ -221,7 +228,9 @@ struct NoProgress {};
 // end the pass means the step loop is broken.
 void check_progress(tsbts_ctx* c, int real, long long pass_steps,
                     long long tau_e) {
-  if (real <= 0 || pass_steps > tau_e - c->t_sys) throw NoProgress{};
+  if (real <= 0 || pass_steps > tau_e - c->t_sys ||
+      (c->cfg.max_pass_steps > 0 && pass_steps > c->cfg.max_pass_steps))
+    throw NoProgress{};
 }
 
 // run one pass; returns the device error bits
@@ -320,14 +329,36 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
     for (;;) {
       bool grow = false;
       long long est = 0;
+      const bool conv = c->cfg.conv_tol > 0.0;
       for (int p = 0; p < c->cfg.n_iter; ++p) {
         if (p > 0) {
+          if (conv)
+            for (int d = 0; d < 3; ++d)
+              ck(cudaMemcpyAsync(c->rlast[d], c->B.r[d],
+                                 sizeof(double) * c->n,
+                                 cudaMemcpyDeviceToDevice, c->s),
+                 "keep pass end");
           launch_copy_state(c->B, c->snap, c->s);
           c->launches += 1;
         }
         const unsigned long long s0 = c->h_ctl->steps;
         const int e = run_pass(c, p, tau_e, est);
         est = (long long)(c->h_ctl->steps - s0);
+        if (!e && conv && p > 0) {
+          // R15: stop once a pass repeats the previous one
+          const long long nrec =
+              std::max(c->h_ctl->slot[0].nrec, c->h_ctl->slot[1].nrec);
+          const int zero = 0;
+          ck(cudaMemcpyAsync(&c->d_ctl->notconv, &zero, sizeof zero,
+                             cudaMemcpyHostToDevice, c->s),
+             "reset convergence flag");
+          launch_converged(c->B, c->H[0], c->H[1], c->rlast, c->cfg.conv_tol,
+                           nrec, c->d_ctl, c->sms, c->s);
+          ck(cudaGetLastError(), "convergence check");
+          c->launches += 1;
+          read_ctl(c);
+          if (!c->h_ctl->notconv) break;
+        }
         if (!e && p + 1 < c->cfg.n_iter) {
           // the next pass interpolates from these records, body-major
           launch_history_to_csr(c->B, c->H[0], c->H[1], c->d_ctl, c->sms,
@@ -429,6 +460,7 @@ void setup_bodies(tsbts_ctx* c, int n) {
   S.tau = dalloc<long long>(L, n);
   S.dt = dalloc<long long>(L, n);
   c->d_ctl = dalloc<Ctl>(L, 1);
+  for (int d = 0; d < 3; ++d) c->rlast[d] = dalloc<double>(L, n);
   c->d_w = dalloc<double>(L, n);
   c->d_eout = dalloc<double>(L, 2);
   c->d_nsplit = dalloc<int>(L, 1);
@@ -436,8 +468,10 @@ void setup_bodies(tsbts_ctx* c, int n) {
   std::memset(c->h_ctl, 0, sizeof(Ctl));
   ck(cudaMemsetAsync(c->d_ctl, 0, sizeof(Ctl), c->s), "memset");
   const long long cap = std::max<long long>(8LL * n, 1LL << 16);
-  alloc_history(c, 0, cap);
-  alloc_history(c, 1, cap);
+  if (c->H[0].cap < cap || c->H[1].cap != c->H[0].cap) {
+    alloc_history(c, 0, cap);
+    alloc_history(c, 1, cap);
+  }
 }
 
 // device arrays of an ensemble: body offsets, cluster of each body, per-
@@ -515,6 +549,9 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     }
     if (c->cfg.era_mode != 0)
       return fail(c, TSBTS_ERR_ARG, "ensembles use a fixed era");
+    if (c->cfg.conv_tol > 0.0)
+      return fail(c, TSBTS_ERR_ARG,
+                  "ensembles run the fixed pass count (conv_tol = 0)");
   }
   if (!(eta > 0.0) || !std::isfinite(eta))
     return fail(c, TSBTS_ERR_ARG, "eta must be finite and > 0");
@@ -525,7 +562,7 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
     return fail(c, TSBTS_ERR_ARG, "era_log2 must be <= k_max");
   try {
     ck(cudaSetDevice(c->cfg.device), "cudaSetDevice");
-    release_all(c);
+    release_all(c, c->inited && c->n == n);
     c->n = (int)n;
     c->eps = eps;
     c->eta = eta;
@@ -666,6 +703,8 @@ void tsbts_config_default(tsbts_config* cfg) {
   cfg->device = 0;
   cfg->stream = nullptr;
   cfg->graph_steps = 32;
+  cfg->conv_tol = 0.0;
+  cfg->max_pass_steps = 0;
 }
 
 int tsbts_create(tsbts_ctx** out, const tsbts_config* cfg) {
@@ -680,6 +719,9 @@ int tsbts_create(tsbts_ctx** out, const tsbts_config* cfg) {
   if (cfg->dyn_min_log2 < 0 || cfg->dyn_min_log2 > 40) return TSBTS_ERR_ARG;
   if (cfg->graph_steps < 0 || cfg->graph_steps > 4096 ||
       (cfg->graph_steps & 1))
+    return TSBTS_ERR_ARG;
+  if (!(cfg->conv_tol >= 0.0) || !std::isfinite(cfg->conv_tol) ||
+      cfg->max_pass_steps < 0)
     return TSBTS_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 ||
@@ -746,7 +788,9 @@ int tsbts_step_era(tsbts_ctx* ctx, double t_end, double* t_reached) {
   } catch (const CudaFail& f) {
     return cuda_fail(ctx, f);
   } catch (const NoProgress&) {
-    return fail(ctx, TSBTS_ERR_TIMEOUT, "block-step loop made no progress");
+    return fail(ctx, TSBTS_ERR_TIMEOUT,
+                "block-step loop made no progress or passed its step "
+                "limit");
   } catch (const std::bad_alloc&) {
     return fail(ctx, TSBTS_ERR_HISTORY, "host out of memory");
   }
@@ -1236,7 +1280,12 @@ int static_setup(int dev, StaticDev** out) {
   StaticDev& d = g_static_dev[dev];
   if (!d.ready) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+      std::fprintf(stderr,
+                   "tsbts_force_static: device address of the scratch "
+                   "array: %s\n",
+                   cudaGetErrorString(e));
       cudaGetLastError();
       return TSBTS_ERR_CUDA;
     }
@@ -1284,10 +1333,17 @@ extern "C" int tsbts_force_static(int precision, int exact_order, int64_t n,
   // Every region is written before it is read in this call (the packed j
   // records, every (split, body) partial of the plan, the split count), so
   // nothing left by an earlier call needs clearing.
+  // a failed launch is reported like tsbts_force's: the step and the CUDA
+  // error on stderr
+  auto failed = [](const char* what, cudaError_t e) {
+    std::fprintf(stderr, "tsbts_force_static: %s: %s\n", what,
+                 cudaGetErrorString(e));
+    return TSBTS_ERR_CUDA;
+  };
   cudaError_t e = launch_pack_aos(
       precision, ni, m, r, v, x, x + ni, x + 2LL * ni, x + 3LL * ni,
       x + 4LL * ni, x + 5LL * ni, x + 6LL * ni, j4, j4 + ni, j4 + 2LL * ni, s);
-  if (e != cudaSuccess) return TSBTS_ERR_CUDA;
+  if (e != cudaSuccess) return failed("pack", e);
   ForceArgs fa{};
   fa.n = ni;
   fa.m = x + 6LL * ni;
@@ -1310,9 +1366,9 @@ extern "C" int tsbts_force_static(int precision, int exact_order, int64_t n,
   fa.plan = plan_force(precision, fa.exact, (int)n_act, ni, fl.grid,
                        kStaticPartDoubles);
   fa.has_plan = 1;
-  if (launch_force(precision, fa, fl, s) != cudaSuccess) return TSBTS_ERR_CUDA;
-  if (launch_force_finalize(part, nsplit, (int)n_act, a, phi, q, s) !=
-      cudaSuccess)
-    return TSBTS_ERR_CUDA;
+  e = launch_force(precision, fa, fl, s);
+  if (e != cudaSuccess) return failed("force", e);
+  e = launch_force_finalize(part, nsplit, (int)n_act, a, phi, q, s);
+  if (e != cudaSuccess) return failed("force finalize", e);
   return TSBTS_OK;
 }

@@ -48,6 +48,8 @@ struct tsbts_ctx {
   std::vector<void*> hist_allocs[2];
   Params P{};
   Ctl* d_ctl = nullptr;
+  double* rlast[3] = {nullptr, nullptr, nullptr};  // positions after the
+                                                   // last pass (R15)
   Ctl* h_ctl = nullptr;  // pinned mirror
   double* d_w = nullptr;
   double* d_eout = nullptr;

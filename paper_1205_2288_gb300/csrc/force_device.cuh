@@ -87,6 +87,49 @@ __device__ __forceinline__ void pair_f64(const F64Tile& T, int t, double xi,
   if (f > s.q) s.q = f;
 }
 
+// 1/sqrt(s2) in FP64 for the j-split path: the FP32 reciprocal square root
+// refined by two Newton-Raphson steps for 1/sqrt (y <- y + y (1 - s2 y^2)/2,
+// each squaring the relative error: 2^-22 -> 2^-44 -> below FP64 rounding),
+// ten FP64 operations instead of a correctly rounded square root and
+// division (the FP64 pipe of this GPU is narrow). s2 outside 1e-36 .. 1e36
+// takes the correctly rounded form.
+__device__ __forceinline__ double rsqrt_f64(double s2) {
+  if (!(s2 > 1e-36 && s2 < 1e36)) return __ddiv_rn(1.0, __dsqrt_rn(s2));
+  double y = (double)rsqrtf((float)s2);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-(s2 * y), y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+
+// The same pair term with the reciprocal square root and fused
+// multiply-adds (j-split path: the sums are not in the oracle's order
+// anyway, and each term agrees with the rounded definition to ~1e-16).
+__device__ __forceinline__ void pair_f64_fast(const F64Tile& T, int t,
+                                              double xi, double yi, double zi,
+                                              double ui, double vi, double wi,
+                                              double eps2, F64Acc& s) {
+  const double dx = T.x[t] - xi;
+  const double dy = T.y[t] - yi;
+  const double dz = T.z[t] - zi;
+  const double s2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+  const double rinv = rsqrt_f64(s2);
+  const double rinv2 = rinv * rinv;
+  const double mr = T.m[t] * rinv;
+  const double f = mr * rinv2;
+  s.ax = fma(f, dx, s.ax);
+  s.ay = fma(f, dy, s.ay);
+  s.az = fma(f, dz, s.az);
+  s.ph -= mr;
+  const double wx = T.u[t] - ui;
+  const double wy = T.v[t] - vi;
+  const double wz = T.w[t] - wi;
+  const double c = fma(wx, wx, fma(wy, wy, wz * wz)) * rinv2;
+  s.q = fmax(s.q, fmax(c, f));
+}
+
 template <int IG>
 __device__ void f64_item(const ForceArgs& A, int n_act, const Plan& P,
     int g, int split, F64Tile& T, double (*red)[kThreads]) {
@@ -125,9 +168,16 @@ __device__ void f64_item(const ForceArgs& A, int n_act, const Plan& P,
         T.m[q] = A.m[j];
       }
       __syncthreads();
-      for (int q = jl; q < cnt; q += JG) {
-        if (jt + q == i) continue;
-        pair_f64(T, q, xi, yi, zi, ui, vi, wi, eps2, s);
+      if (A.exact) {
+        for (int q = jl; q < cnt; q += JG) {
+          if (jt + q == i) continue;
+          pair_f64(T, q, xi, yi, zi, ui, vi, wi, eps2, s);
+        }
+      } else {
+        for (int q = jl; q < cnt; q += JG) {
+          if (jt + q == i) continue;
+          pair_f64_fast(T, q, xi, yi, zi, ui, vi, wi, eps2, s);
+        }
       }
     }
     if constexpr (JG > 1) {

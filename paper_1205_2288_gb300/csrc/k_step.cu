@@ -408,6 +408,35 @@ __global__ void history_scatter_kernel(History src, History dst,
   }
 }
 
+// ---------------------------------------------------------------------
+// Converged iteration (reading R15): after pass p >= 1, the pass repeated
+// pass p - 1 when every body has as many records at the same times (the
+// running pass's append buffer against the previous pass's CSR records)
+// and every body's position at the end of the pass is within tol of the
+// end of pass p - 1 (rlast). Any difference sets ctl->notconv.
+// ---------------------------------------------------------------------
+__global__ void converged_kernel(Bodies B, History cur, History prev,
+                                 const double* rl0, const double* rl1,
+                                 const double* rl2, double tol,
+                                 long long nrec, Ctl* ctl) {
+  int bad = 0;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = tid; i < B.n; i += stride) {
+    if (B.hcnt[i] != B.hoff[i + 1] - B.hoff[i]) bad = 1;
+    if (!(fabs(B.r[0][i] - rl0[i]) < tol) || !(fabs(B.r[1][i] - rl1[i]) < tol) ||
+        !(fabs(B.r[2][i] - rl2[i]) < tol))
+      bad = 1;
+  }
+  for (long long r = tid; r < nrec; r += stride) {
+    const int b = cur.body[r], q = cur.seq[r];
+    const int cnt = B.hoff[b + 1] - B.hoff[b];
+    if (q >= cnt || cur.tau[r] != prev.tau[B.hoff[b] + q]) bad = 1;
+  }
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0)
+    atomicOr(&ctl->notconv, 1);
+}
+
 __global__ void copy_state_kernel(Bodies dst, Bodies src) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < dst.n;
        i += gridDim.x * blockDim.x) {
@@ -649,6 +678,13 @@ cudaError_t launch_correct(const Bodies& B, const Params& P,
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, correct_kernel, B, P, HA, HB, p);
+}
+
+void launch_converged(const Bodies& B, const History& cur,
+                      const History& prev, double* const rlast[3], double tol,
+                      long long nrec, Ctl* ctl, int sms, cudaStream_t s) {
+  converged_kernel<<<sms * 4, 256, 0, s>>>(B, cur, prev, rlast[0], rlast[1],
+                                           rlast[2], tol, nrec, ctl);
 }
 
 void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s) {

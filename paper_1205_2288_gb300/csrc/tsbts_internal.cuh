@@ -67,6 +67,7 @@ struct Ctl {
   int pass;     // pass index within the era
   int era;      // era index (schedule log)
   int err;      // kErr* bits
+  int notconv;  // converged-iteration check: nonzero if the pass differs
   int hist[kMaxLevels];  // bodies per level k (dt = 2^-k)
 };
 

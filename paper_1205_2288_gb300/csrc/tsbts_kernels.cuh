@@ -19,6 +19,11 @@ cudaError_t launch_correct(const Bodies& B, const Params& P,
                            const History& HA, const History& HB, int p,
                            int grid, bool pdl, cudaStream_t s);
 void launch_copy_state(const Bodies& dst, const Bodies& src, cudaStream_t s);
+// converged iteration: ctl->notconv |= (this pass differs from the last);
+// nrec = records of the running pass, rlast = positions after the last pass
+void launch_converged(const Bodies& B, const History& cur,
+                      const History& prev, double* const rlast[3], double tol,
+                      long long nrec, Ctl* ctl, int sms, cudaStream_t s);
 // the running pass's appended records -> previous-pass records in CSR order
 void launch_history_to_csr(const Bodies& B, const History& append,
                            const History& csr, const Ctl* ctl, int sms,

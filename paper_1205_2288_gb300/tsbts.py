@@ -53,7 +53,8 @@ class tsbts_config(C.Structure):
                 ("era_mode", C.c_int), ("era_log2", C.c_int),
                 ("dyn_min_log2", C.c_int), ("k_max", C.c_int),
                 ("exact_order", C.c_int), ("device", C.c_int),
-                ("stream", C.c_void_p), ("graph_steps", C.c_int)]
+                ("stream", C.c_void_p), ("graph_steps", C.c_int),
+                ("conv_tol", C.c_double), ("max_pass_steps", I64)]
 
 
 class tsbts_stats(C.Structure):
@@ -291,13 +292,37 @@ def tsbts_destroy(ctx):
         lib().tsbts_destroy(ctx)
 
 
+def _check_force_tensors(name, m, r, v, idx, a, phi, q):
+    """The kernels read and write exactly these shapes and dtypes on the
+    current device; anything else is refused before the library is
+    called. Index values must lie in [0, n) (not checked here: that would
+    synchronise the device on every call)."""
+    import torch
+    dev = torch.cuda.current_device()
+    for t in (m, r, v, idx, a, phi, q):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} takes contiguous CUDA tensors")
+        if t.device.index != dev:
+            raise ValueError(f"{name}: tensors must be on the current "
+                             f"device cuda:{dev}")
+    for t in (m, r, v, a, phi, q):
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name}: m, r, v, a, phi, q must be float64")
+    if idx.dtype != torch.int32:
+        raise ValueError(f"{name}: idx must be int32")
+    n, na = m.shape[0], idx.shape[0]
+    if (m.dim() != 1 or tuple(r.shape) != (n, 3) or tuple(v.shape) != (n, 3)
+            or idx.dim() != 1 or tuple(a.shape) != (na, 3)
+            or tuple(phi.shape) != (na,) or tuple(q.shape) != (na,)):
+        raise ValueError(f"{name}: shapes must be m (n,), r and v (n, 3), "
+                         "idx (n_act,), a (n_act, 3), phi and q (n_act,)")
+
+
 def tsbts_force(precision, m, r, v, eps, idx, a, phi, q, exact_order=-1,
                 stream=None):
     """Device-pointer force call on torch CUDA tensors (see tsbts.h)."""
     import torch
-    for t in (m, r, v, idx, a, phi, q):
-        if not t.is_cuda or not t.is_contiguous():
-            raise ValueError("tsbts_force takes contiguous CUDA tensors")
+    _check_force_tensors("tsbts_force", m, r, v, idx, a, phi, q)
     if stream is None:
         stream = torch.cuda.current_stream(m.device).cuda_stream
     _check(lib().tsbts_force(int(precision), int(exact_order), m.shape[0],
@@ -312,9 +337,7 @@ def tsbts_force_static(precision, m, r, v, eps, idx, a, phi, q,
     """tsbts_force without device allocation (see tsbts.h): scratch lives
     in a fixed array inside the library; n, n_act <= 65536."""
     import torch
-    for t in (m, r, v, idx, a, phi, q):
-        if not t.is_cuda or not t.is_contiguous():
-            raise ValueError("tsbts_force_static takes contiguous CUDA tensors")
+    _check_force_tensors("tsbts_force_static", m, r, v, idx, a, phi, q)
     if stream is None:
         stream = torch.cuda.current_stream(m.device).cuda_stream
     _check(lib().tsbts_force_static(int(precision), int(exact_order),
@@ -451,8 +474,11 @@ class Simulation:
 
     def __init__(self, m, r, v, *, eps, eta, dt_max, precision=TSBTS_FP64,
                  n_iter=3, era_mode=0, era_log2=3, dyn_min_log2=3, k_max=20,
-                 exact_order=-1, device=0, stream=None, graph_steps=32):
+                 exact_order=-1, device=0, stream=None, graph_steps=32,
+                 conv_tol=0.0, max_pass_steps=0):
         cfg = tsbts_config_default()
+        cfg.conv_tol = conv_tol
+        cfg.max_pass_steps = max_pass_steps
         cfg.precision = precision
         cfg.n_iter = n_iter
         cfg.era_mode = era_mode

@@ -2,7 +2,8 @@
 softening) with the FP64 oracle, through the C ABI entry tsbts_force.
 
 FP64 with ascending-j order is bit-identical to the oracle; the FP64 j-split
-differs only in summation order; the mixed path (FP32 pair terms on
+differs in summation order and forms 1/s by a refined reciprocal square
+root (to rounding); the mixed path (FP32 pair terms on
 double-single coordinates) must keep every a_i within 1e-6 of the
 oracle relative to the sum of the pair magnitudes sum_j m_j / s_ij^2, the
 bulk of |a_i| relative errors below 1e-6, phi within 1e-6 relative and q
@@ -83,8 +84,9 @@ def test_fp64_jsplit_matches_to_rounding(torch_cuda, orc, n, n_act, eps, seed):
     scale = pair_magnitude_sum(m, r, eps, idx)
     assert (np.abs(a - ao).max(1) / scale).max() < 1e-13
     np.testing.assert_allclose(phi, phio, rtol=1e-13)
-    # q is a max of identically rounded pair terms: exact in any order
-    np.testing.assert_array_equal(q, qo)
+    # the j-split path forms 1/s from a refined reciprocal square root, so
+    # q's terms agree with the rounded definition to a few ulps
+    np.testing.assert_allclose(q, qo, rtol=1e-14)
 
 
 @pytest.mark.parametrize("n,n_act,eps,seed", CASES + [(20000, 3, 0.01, 5),
@@ -98,7 +100,10 @@ def test_mixed_within_tolerance(torch_cuda, orc, n, n_act, eps, seed):
     err_scaled = np.abs(a - ao).max(1) / scale
     assert err_scaled.max() < 1e-6
     rel = np.linalg.norm(a - ao, axis=1) / np.linalg.norm(ao, axis=1)
-    assert np.quantile(rel, 0.99) < 1e-6
+    # reading R12: the relative error of |a_i| at the 99.9th percentile
+    # (near the cluster centre |a_i| cancels; those bodies are held to the
+    # scaled bound above)
+    assert np.quantile(rel, 0.999) < 1e-6
     np.testing.assert_allclose(phi, phio, rtol=1e-6)
     np.testing.assert_allclose(q, qo, rtol=2e-6)
 
@@ -123,20 +128,38 @@ def test_edge_cases(torch_cuda, orc):
     e = torch.zeros(0, dtype=torch.int32, device="cuda:0")
     z = torch.zeros(0, dtype=torch.float64, device="cuda:0")
     tsbts.tsbts_force(0, tm, tr, tr, 0.1, e, z.view(0, 3), z, z)
+    # the binding refuses what the kernels would misread: a wrong dtype,
+    # index type or shape never reaches the library
+    one = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    a1 = torch.zeros(1, 3, dtype=torch.float64, device="cuda:0")
+    p1 = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    bad = [dict(m=tm.float()), dict(idx=one.long()), dict(r=tr[:, :2].contiguous()),
+           dict(a=torch.zeros(2, 3, dtype=torch.float64, device="cuda:0"))]
+    for fn in (tsbts.tsbts_force, tsbts.tsbts_force_static):
+        for b in bad:
+            kw = dict(m=tm, r=tr, v=tr, idx=one, a=a1, phi=p1, q=p1)
+            kw.update(b)
+            with pytest.raises(ValueError):
+                fn(1, kw["m"], kw["r"], kw["v"], 0.1, kw["idx"], kw["a"],
+                   kw["phi"], kw["q"])
 
 
 def test_full_size_sampled(torch_cuda, orc):
     """Plummer n = 131072, eps = 1/512: the active-set sweep of the force
-    benchmark; 48 sampled outputs per set are checked against the oracle."""
+    benchmark; up to 1024 sampled outputs per set are checked against the
+    oracle, scaled (every one) and relative (99.9th percentile, R12)."""
     n, eps = 131072, 1 / 512
     m, r, v = inputs.plummer(n, 0)
+    orc.set_threads(8)
     for n_act in (1, 32, 1024, 32768, n):
         idx = inputs.active_subset(n, n_act, 1000 + n_act)
         a, phi, q = gpu_force(torch_cuda, tsbts.TSBTS_MIXED, m, r, v, eps, idx)
-        pick = np.unique(np.linspace(0, n_act - 1, 48).astype(int))
+        pick = np.unique(np.linspace(0, n_act - 1, 1024).astype(int))
         ao, phio, qo = orc.forces(m, r, v, eps, idx[pick])
         scale = pair_magnitude_sum(m, r, eps, idx[pick])
         assert (np.abs(a[pick] - ao).max(1) / scale).max() < 1e-6
+        rel = np.linalg.norm(a[pick] - ao, axis=1) / np.linalg.norm(ao, axis=1)
+        assert np.quantile(rel, 0.999) < 1e-6
         np.testing.assert_allclose(phi[pick], phio, rtol=1e-6)
         np.testing.assert_allclose(q[pick], qo, rtol=2e-6)
         assert np.isfinite(a).all() and np.isfinite(phi).all()

@@ -261,3 +261,78 @@ def test_force_timing_counts_real_steps(orc, graph_steps):
     assert st["force_ms"] > 0
     assert_same_state(o, g)
     g.close()
+
+
+@pytest.mark.parametrize("era_mode,tol", [(0, 1e9), (1, 1e9), (0, 1e-6),
+                                          (1, 1e-300)])
+def test_converged_iteration_bit_exact(orc, era_mode, tol):
+    """Reading R15 (converged iteration): an era stops after pass p >= 1
+    once pass p took the same block steps as pass p - 1 and its end
+    positions are within conv_tol of them, at most n_iter passes. In FP64
+    the GPU takes the same decisions as the oracle, era by era: the same
+    passes, schedule and state, bit for bit. tol = 1e9 lets the schedule
+    decide; 1e-300 cannot be met, so every pass runs."""
+    m, r, v = inputs.plummer(160, 41)
+    kw = dict(eps=0.02, eta=0.05, dt_max=1 / 8, n_iter=6, era_mode=era_mode,
+              era_log2=3, k_max=20, conv_tol=tol)
+    o, g, _, _ = run_pair(orc, m, r, v, 0.375, **kw)
+    assert g.stats()["passes"] == o.stats()["passes"]
+    if tol == 1e-300:
+        assert o.stats()["passes"] == 6 * o.stats()["eras"]
+    assert_same_schedule(o, g)
+    assert_same_state(o, g)
+    assert g.energy() == o.energy()
+
+
+def test_shared_step_converges_after_two_passes():
+    """Every body active at every step: pass 1 repeats pass 0 exactly, so
+    with any tolerance the era stops after two passes and the state is the
+    one-pass state (as the oracle's pin shows)."""
+    m, r, v = inputs.plummer(40, 2)
+    kw = dict(eps=0.05, eta=0.1, dt_max=2.0 ** -7, era_mode=0, era_log2=4,
+              k_max=7)
+    a = tsbts.Simulation(m, r, v, n_iter=6, conv_tol=1e-300, **kw)
+    a.step_era(0.25)
+    b = tsbts.Simulation(m, r, v, n_iter=1, **kw)
+    b.step_era(0.25)
+    st = a.stats()
+    assert st["passes"] == 2 * st["eras"]
+    sa, sb = a.state(), b.state()
+    for key in ("r", "v", "a", "tau", "dt"):
+        np.testing.assert_array_equal(sa[key], sb[key])
+
+
+def test_pass_step_limit_gives_timeout_and_poisons():
+    """The host watchdog of the block-step loop: a pass that takes more
+    block steps than max_pass_steps stops with TSBTS_ERR_TIMEOUT (no GPU
+    wait is involved: the loop's chunks return and the host counts them),
+    the context refuses further calls, and a new context on the same
+    device runs normally."""
+    m, r, v = inputs.plummer(256, 3)
+    kw = dict(eps=0.01, eta=0.01, dt_max=1 / 8, n_iter=3, era_mode=0,
+              era_log2=3, k_max=20)
+    g = tsbts.Simulation(m, r, v, max_pass_steps=8, graph_steps=16, **kw)
+    with pytest.raises(tsbts.TsbtsError) as e:
+        g.step_era(0.125)
+    assert e.value.code == tsbts.TSBTS_ERR_TIMEOUT
+    with pytest.raises(tsbts.TsbtsError) as e:
+        g.energy()
+    assert e.value.code == tsbts.TSBTS_ERR_STATE
+    g.close()
+    ok = tsbts.Simulation(m, r, v, **kw)
+    ok.step_era(0.125)
+    assert ok.stats()["block_steps"] > 8
+    ok.close()
+
+
+def test_step_underflow_count_matches_oracle(orc):
+    """Reading R10: steps below 2^-k_max are clamped to one tick and
+    counted; with k_max = 8 a tight Plummer cluster underflows, and the
+    GPU counts the same clamps as the oracle (FP64, bit-exact run)."""
+    m, r, v = inputs.plummer(96, 12)
+    kw = dict(eps=0.002, eta=0.05, dt_max=1 / 8, n_iter=3, era_mode=0,
+              era_log2=3, k_max=8)
+    o, g, _, _ = run_pair(orc, m, r, v, 0.25, **kw)
+    assert o.stats()["underflow"] > 0
+    assert g.stats()["dt_underflow"] == o.stats()["underflow"]
+    assert_same_state(o, g)
