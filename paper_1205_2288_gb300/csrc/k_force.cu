@@ -393,7 +393,8 @@ cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
   // each candidate: one warm-up launch, then kReps batches of kBatch
   // back-to-back launches, each batch bracketed by events (the event clock
   // ticks in microseconds, coarser than a small launch); its time is the
-  // median batch over kBatch (robust to a stray slow batch)
+  // median batch over kBatch (robust to a stray slow batch). A candidate
+  // whose warm-up is over 4x the best so far is dropped.
   constexpr int kReps = 3;
   constexpr int kBatch = 8;
   cudaEvent_t ev[kReps + 1];
@@ -416,10 +417,20 @@ cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
       fa.plans = nullptr;
       fa.plan = p;
       fa.has_plan = 1;
+      // the warm-up launch, timed, sets the batch: launches of more than
+      // ~0.1 ms are timed one at a time
+      cudaEventRecord(ev[0], s);
       launch_force(1, fa, fl, s);
+      cudaEventRecord(ev[1], s);
+      err = cudaEventSynchronize(ev[1]);
+      if (err != cudaSuccess) break;
+      float warm = 0;
+      cudaEventElapsedTime(&warm, ev[0], ev[1]);
+      const int batch = warm > 0.1f ? 1 : kBatch;
+      if (warm > 4.0f * best_ms) continue;  // far slower than the best
       for (int r = 0; r < kReps; ++r) {
         cudaEventRecord(ev[r], s);
-        for (int q = 0; q < kBatch; ++q) launch_force(1, fa, fl, s);
+        for (int q = 0; q < batch; ++q) launch_force(1, fa, fl, s);
       }
       cudaEventRecord(ev[kReps], s);
       err = cudaEventSynchronize(ev[kReps]);
@@ -427,7 +438,7 @@ cudaError_t autotune_mixed_plans(int device, const ForceArgs& base,
       float t[kReps];
       for (int r = 0; r < kReps; ++r) cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
       std::sort(t, t + kReps);
-      const float ms = t[kReps / 2] / kBatch;
+      const float ms = t[kReps / 2] / batch;
       if (ms < best_ms) {
         best_ms = ms;
         best[bi] = p;
