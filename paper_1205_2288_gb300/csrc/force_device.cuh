@@ -208,6 +208,77 @@ __device__ void f64_item(const ForceArgs& A, int n_act, const Plan& P,
   }
 }
 
+// FP64 with ascending-j sums for a few active bodies, one body per block:
+// the block's threads compute the pair terms of kThreads consecutive j in
+// parallel (the correctly rounded square root and divisions are the long
+// latency) and thread 0 then adds them in ascending j, the same rounded
+// operations in the same order as one thread running the whole loop. The
+// self pair contributes exact zeros (a sum that starts at +0 is never -0,
+// so adding +0 leaves it unchanged). q is a maximum, exact in any order.
+__device__ inline void f64_item_exact1(const ForceArgs& A, int n_act, int k,
+                                double (*red)[kThreads]) {
+  const int t = threadIdx.x;
+  const int i = A.idx[k];
+  const double xi = A.x[0][i], yi = A.x[1][i], zi = A.x[2][i];
+  const double ui = A.w[0][i], vi = A.w[1][i], wi = A.w[2][i];
+  const double eps2 = A.eps2;
+  F64Acc s = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double ql = 0.0;
+  for (int jt = 0; jt < A.n; jt += kThreads) {
+    const int j = jt + t;
+    double tx = 0.0, ty = 0.0, tz = 0.0, tp = 0.0;
+    if (j < A.n && j != i) {
+      const double dx = __dsub_rn(A.x[0][j], xi);
+      const double dy = __dsub_rn(A.x[1][j], yi);
+      const double dz = __dsub_rn(A.x[2][j], zi);
+      const double s2 = __dadd_rn(
+          __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                    __dmul_rn(dz, dz)),
+          eps2);
+      const double sq = __dsqrt_rn(s2);
+      const double mj = A.m[j];
+      const double f = __ddiv_rn(mj, __dmul_rn(s2, sq));
+      tx = __dmul_rn(f, dx);
+      ty = __dmul_rn(f, dy);
+      tz = __dmul_rn(f, dz);
+      tp = __ddiv_rn(mj, sq);
+      const double wx = __dsub_rn(A.w[0][j], ui);
+      const double wy = __dsub_rn(A.w[1][j], vi);
+      const double wz = __dsub_rn(A.w[2][j], wi);
+      const double c = __ddiv_rn(
+          __dadd_rn(__dadd_rn(__dmul_rn(wx, wx), __dmul_rn(wy, wy)),
+                    __dmul_rn(wz, wz)),
+          s2);
+      if (c > ql) ql = c;
+      if (f > ql) ql = f;
+    }
+    __syncthreads();  // the previous tile's terms have been added
+    red[0][t] = tx;
+    red[1][t] = ty;
+    red[2][t] = tz;
+    red[3][t] = tp;
+    __syncthreads();
+    if (t == 0) {
+      const int cnt = min(kThreads, A.n - jt);
+      for (int q = 0; q < cnt; ++q) {
+        s.ax = __dadd_rn(s.ax, red[0][q]);
+        s.ay = __dadd_rn(s.ay, red[1][q]);
+        s.az = __dadd_rn(s.az, red[2][q]);
+        s.ph = __dsub_rn(s.ph, red[3][q]);
+      }
+    }
+  }
+  __syncthreads();
+  red[4][t] = ql;
+  __syncthreads();
+  for (int half = kThreads / 2; half >= 1; half >>= 1) {
+    if (t < half) red[4][t] = fmax(red[4][t], red[4][t + half]);
+    __syncthreads();
+  }
+  if (t == 0) write_partial(A, n_act, 0, k, s.ax, s.ay, s.az, s.ph, red[4][0]);
+  __syncthreads();  // red is reused by the block's next body
+}
+
 template <int IG>
 __device__ void f64_items(const ForceArgs& A, int n_act, const Plan& P,
                           F64Tile& T, double (*red)[kThreads]) {

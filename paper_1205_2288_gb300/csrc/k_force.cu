@@ -40,6 +40,10 @@ namespace tsbts {
 Plan plan_force(int precision, int exact, int n_act, int n, int grid,
                 long long part_cap) {
   Plan best = {kThreads, (n_act + kThreads - 1) / kThreads, 1, n};
+  // ascending-j sums: one body per block while the bodies fit the grid
+  // (latency-bound: the block computes the terms, one thread adds them),
+  // one body per thread beyond that (throughput-bound)
+  if (exact && n_act > 0 && n_act <= grid) return Plan{1, n_act, 1, n, 0};
   if (exact || n_act <= 0) return best;
   const int lane_min = precision ? kLaneMinMix : kLaneMinF64;
   double best_cost = 1e300;
@@ -74,8 +78,8 @@ __device__ __forceinline__ Plan make_plan(int n_act, int n, int grid,
   Plan p;
   p.direct = 0;
   if (exact) {
-    p.ig = kThreads;
-    p.n_g = (n_act + kThreads - 1) / kThreads;
+    p.ig = n_act <= grid ? 1 : kThreads;
+    p.n_g = (n_act + p.ig - 1) / p.ig;
     p.S = 1;
     p.chunk = n;
     return p;
@@ -158,6 +162,12 @@ __global__ void __launch_bounds__(kThreads)
     *A.nsplit_out = P.S;
   __shared__ F64Tile T;
   __shared__ double red[5][kThreads];
+  if (A.exact && P.ig == 1) {
+    // few bodies, ascending-j sums: one body per block
+    for (int w = blockIdx.x; w < n_act; w += gridDim.x)
+      f64_item_exact1(A, n_act, w, red);
+    return;
+  }
   switch (P.ig) {
     case 128: f64_items<128>(A, n_act, P, T, red); break;
     case 64: f64_items<64>(A, n_act, P, T, red); break;
