@@ -660,7 +660,10 @@ __device__ __forceinline__ void pair_mixed_g(const MixI& I, const float4 h,
 // Narrow groups without shared-memory staging: j-lane jl of a body reads
 // j = j0 + jl, j0 + jl + JG, ... straight from global memory (the j records
 // are L2-resident), so a small active set costs no block-wide tile loads.
-template <int IG>
+// BATCH j records per lane are loaded in one batch before any is used, so
+// a small item waits for a few round trips to L2, not one per j; BATCH = 1
+// keeps the register budget of kernels that hold more state (ensembles).
+template <int IG, int BATCH = kDirectBatch>
 __device__ void mixed_direct_item(const ForceArgs& A, int n_act, const Plan& P,
     int g, int split, float (*red)[kThreads]) {
   constexpr int JG = kThreads / IG;
@@ -683,13 +686,26 @@ __device__ void mixed_direct_item(const ForceArgs& A, int n_act, const Plan& P,
     float ax = 0, ay = 0, az = 0, ph = 0;
     const int j0 = split * P.chunk;
     const int j1 = min(A.n, j0 + P.chunk);
-    // kDirectBatch j records per lane are loaded in one batch before any is
-    // used, so a small item waits for one round trip to L2, not one per j
     int cnt = 0;
-    for (int jb = j0 + jl; jb < j1; jb += JG * kDirectBatch) {
-      float4 h[kDirectBatch], l[kDirectBatch], vv[kDirectBatch];
+    if constexpr (BATCH == 1) {
+#pragma unroll 4
+      for (int j = j0 + jl; j < j1; j += JG) {
+        const float4 h = A.jhi[j], l = A.jlo[j], vv = A.jv[j];
+        if (j != i) pair_mixed_g(I, h, l, vv, eps2, ax, ay, az, ph, q);
+        if (++cnt == kTileMix) {
+          cnt = 0;
+          ds_add(sx, ax);
+          ds_add(sy, ay);
+          ds_add(sz, az);
+          ds_add(sp, ph);
+          ax = ay = az = ph = 0.f;
+        }
+      }
+    }
+    for (int jb = j0 + jl; BATCH > 1 && jb < j1; jb += JG * BATCH) {
+      float4 h[BATCH], l[BATCH], vv[BATCH];
 #pragma unroll
-      for (int u = 0; u < kDirectBatch; ++u) {
+      for (int u = 0; u < BATCH; ++u) {
         const int j = jb + u * JG;
         if (j < j1) {
           h[u] = __ldg(A.jhi + j);
@@ -698,12 +714,12 @@ __device__ void mixed_direct_item(const ForceArgs& A, int n_act, const Plan& P,
         }
       }
 #pragma unroll
-      for (int u = 0; u < kDirectBatch; ++u) {
+      for (int u = 0; u < BATCH; ++u) {
         const int j = jb + u * JG;
         if (j < j1 && j != i)
           pair_mixed_g(I, h[u], l[u], vv[u], eps2, ax, ay, az, ph, q);
       }
-      cnt += kDirectBatch;
+      cnt += BATCH;
       if (cnt >= kTileMix) {
         cnt = 0;
         ds_add(sx, ax);

@@ -307,11 +307,11 @@ __global__ void __launch_bounds__(kThreads, kMixMinBlocks)
     const ForceArgs A = cluster_args(B, E, c, part, p, n_act, 0);
     if (p.direct) {
       switch (p.ig) {
-        case 16: mixed_direct_item<16>(A, n_act, p, g, split, red); break;
-        case 8: mixed_direct_item<8>(A, n_act, p, g, split, red); break;
-        case 4: mixed_direct_item<4>(A, n_act, p, g, split, red); break;
-        case 2: mixed_direct_item<2>(A, n_act, p, g, split, red); break;
-        default: mixed_direct_item<1>(A, n_act, p, g, split, red); break;
+        case 16: mixed_direct_item<16, 1>(A, n_act, p, g, split, red); break;
+        case 8: mixed_direct_item<8, 1>(A, n_act, p, g, split, red); break;
+        case 4: mixed_direct_item<4, 1>(A, n_act, p, g, split, red); break;
+        case 2: mixed_direct_item<2, 1>(A, n_act, p, g, split, red); break;
+        default: mixed_direct_item<1, 1>(A, n_act, p, g, split, red); break;
       }
     } else {
       switch (p.ig) {

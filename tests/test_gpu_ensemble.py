@@ -125,3 +125,60 @@ def test_ensemble_argument_errors():
         assert e.value.code == tsbts.TSBTS_ERR_ARG
     finally:
         tsbts.tsbts_destroy(ctx)
+
+
+def config4_subset(count=32, seed=7):
+    """A seeded subset of the 512-cluster workload (sizes log-uniform in
+    [64, 4096], Salpeter masses, eps_c = 4 / N_c): the clusters' own
+    bodies, offsets and softenings."""
+    off, m, r, v, eps = inputs.ensemble(512, seed=0)
+    pick = np.sort(np.random.default_rng(seed).choice(512, count,
+                                                      replace=False))
+    sizes = np.diff(off)[pick]
+    sub_off = np.zeros(count + 1, np.int64)
+    sub_off[1:] = np.cumsum(sizes)
+    take = np.concatenate([np.arange(off[c], off[c + 1]) for c in pick])
+    return sub_off, m[take], r[take], v[take], eps[pick]
+
+
+KW4 = dict(eta=0.01, dt_max=1 / 8, n_iter=3, era_log2=3, k_max=20)
+
+
+def test_config4_subset_fp64_bit_exact(orc):
+    """32 clusters of the 512-cluster configuration, FP64 with ascending-j
+    sums, over t = 0..1/64: every cluster's state and energy are the
+    oracle's, bit for bit."""
+    off, m, r, v, eps = config4_subset()
+    assert np.diff(off).max() > 1000 and np.diff(off).min() < 200
+    orc.set_threads(16)
+    ref = oracle_clusters(orc, off, m, r, v, eps, 1 / 64, **KW4)
+    g = tsbts.Ensemble(off, m, r, v, eps=eps, exact_order=1, **KW4)
+    g.step_era(1 / 64)
+    st = g.state()
+    ek, ep = g.cluster_energy()
+    for c in range(len(off) - 1):
+        a, b = off[c], off[c + 1]
+        so, _, e1, _ = ref[c]
+        for key in ("r", "v", "a", "tau", "dt"):
+            np.testing.assert_array_equal(st[key][a:b], so[key],
+                                          err_msg=f"cluster {c} {key}")
+        assert (ek[c], ep[c]) == e1
+    assert g.stats()["interactions"] == sum(x[3]["interactions"] for x in ref)
+
+
+def test_config4_subset_mixed_energy_bar(orc):
+    """The same clusters in mixed precision: each cluster's relative energy
+    error within twice the oracle's (plus the FP32 force-noise floor)."""
+    off, m, r, v, eps = config4_subset()
+    orc.set_threads(16)
+    ref = oracle_clusters(orc, off, m, r, v, eps, 1 / 64, **KW4)
+    g = tsbts.Ensemble(off, m, r, v, eps=eps, precision=tsbts.TSBTS_MIXED,
+                       **KW4)
+    ek0, ep0 = g.cluster_energy()
+    g.step_era(1 / 64)
+    ek, ep = g.cluster_energy()
+    for c in range(len(off) - 1):
+        _, e0, e1, _ = ref[c]
+        de_o = abs(sum(e1) / sum(e0) - 1.0)
+        de_g = abs((ek[c] + ep[c]) / (ek0[c] + ep0[c]) - 1.0)
+        assert de_g <= 2 * de_o + 1e-7, (c, de_g, de_o)
