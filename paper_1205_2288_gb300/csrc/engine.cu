@@ -516,11 +516,12 @@ void setup_ensemble(tsbts_ctx* c, const EnsInput& in) {
   E.item_off = dalloc<int>(L, nc + 1);
   E.act_base = dalloc<int>(L, nc + 1);
   E.part_off = dalloc<long long>(L, nc + 1);
-  E.totals = dalloc<int>(L, 4);
-  ck(cudaMemsetAsync(E.totals, 0, sizeof(int) * 4, c->s), "memset");
+  E.totals = dalloc<int>(L, 8);
+  ck(cudaMemsetAsync(E.totals, 0, sizeof(int) * 8, c->s), "memset");
   c->d_ek = dalloc<double>(L, nc);
   c->d_ep = dalloc<double>(L, nc);
   c->efl = ens_force_launch_shape(c->cfg.precision, c->cfg.device);
+  E.part_cap = c->B.part_cap;
   c->nc = nc;
   c->ensemble = true;
 }

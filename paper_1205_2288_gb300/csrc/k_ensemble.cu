@@ -141,7 +141,26 @@ __global__ void ens_predict_kernel(Bodies B, Params P, Ens E, History prev) {
 // ---------------------------------------------------------------------
 // plan: per-cluster plans and the work-item layout (one block)
 // ---------------------------------------------------------------------
-__device__ __forceinline__ Plan ens_plan_for(int n_act, int n, int exact) {
+// The work of one global step is spread over about kEnsTargetItems work
+// items of similar size: a cluster with w = n_act * N_c interactions gets
+// its i-groups (ig = n_act rounded up to a power of two, at most 128) and
+// as many j-splits as w / (W / kEnsTargetItems) asks for (W = the step's
+// total), within a floor of j per lane; so a large cluster's step spreads
+// over the whole grid instead of a few blocks. Measured on the 512-cluster
+// workload (t = 0..1/8): 912, 1824 and 3648 target items gave 167, 180 and
+// 185 G interactions/s, a floor of 32 j per lane instead of 8 was slower.
+#ifndef TSBTS_ENS_ITEMS
+#define TSBTS_ENS_ITEMS 3648
+#endif
+#ifndef TSBTS_ENS_LANE_MIN
+#define TSBTS_ENS_LANE_MIN 8
+#endif
+constexpr int kEnsTargetItems = TSBTS_ENS_ITEMS;
+constexpr int kEnsLaneMin = TSBTS_ENS_LANE_MIN;
+constexpr int kEnsSplitCap = 64;
+
+__device__ __forceinline__ Plan ens_plan_for(int n_act, int n, int exact,
+                                             double per_item) {
   Plan p;
   p.S = 1;
   p.chunk = (n + 1) & ~1;
@@ -155,6 +174,16 @@ __device__ __forceinline__ Plan ens_plan_for(int n_act, int n, int exact) {
     p.direct = ig <= 16;
   }
   p.n_g = (n_act + p.ig - 1) / p.ig;
+  if (!exact && n_act > 0 && per_item > 0.0) {
+    const double w = (double)n_act * (double)n;
+    int S = (int)ceil(w / per_item / p.n_g);
+    const int jg = 128 / p.ig;
+    int smax = n / (jg * kEnsLaneMin);
+    smax = smax < 1 ? 1 : (smax > kEnsSplitCap ? kEnsSplitCap : smax);
+    S = S < 1 ? 1 : (S > smax ? smax : S);
+    p.S = S;
+    p.chunk = (((n + S - 1) / S) + 1) & ~1;
+  }
   return p;
 }
 
@@ -191,13 +220,42 @@ __global__ void __launch_bounds__(kPlanThreads)
   __shared__ int c_items, c_nact;
   __shared__ long long c_part;
   __shared__ unsigned long long s_inter;
+  __shared__ int s_fallback;
   if (threadIdx.x == 0) {
     c_items = 0;
     c_nact = 0;
     c_part = 0;
     s_inter = 0;
+    s_fallback = 0;
   }
   __syncthreads();
+  // the step's total work sets the size of a work item
+  for (int c = threadIdx.x; c < E.nc; c += blockDim.x)
+    if (E.tau_next[c] != LLONG_MAX && E.cnt[c] > 0)
+      atomicAdd(&s_inter, (unsigned long long)E.cnt[c] *
+                              (unsigned long long)(E.off[c + 1] - E.off[c]));
+  __syncthreads();
+  const unsigned long long total_w = s_inter;
+  double per_item = (double)total_w / kEnsTargetItems;
+  // the split partials of the step must fit the partial-sum buffer
+  // (else every cluster takes one split)
+  {
+    __shared__ unsigned long long s_parts;
+    if (threadIdx.x == 0) s_parts = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < E.nc; c += blockDim.x) {
+      if (E.tau_next[c] == LLONG_MAX) continue;
+      const int na = E.cnt[c];
+      const Plan p = ens_plan_for(na, E.off[c + 1] - E.off[c], P.exact,
+                                  per_item);
+      atomicAdd(&s_parts, 5ULL * p.S * (unsigned long long)na);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_parts > (unsigned long long)E.part_cap)
+      s_fallback = 1;
+    __syncthreads();
+    if (s_fallback) per_item = 0.0;
+  }
   for (int base = 0; base < E.nc; base += kPlanThreads) {
     const int c = base + threadIdx.x;
     const bool valid = c < E.nc;
@@ -206,12 +264,10 @@ __global__ void __launch_bounds__(kPlanThreads)
     if (valid) {
       nb = E.off[c + 1] - E.off[c];
       if (E.tau_next[c] != LLONG_MAX) n_act = E.cnt[c];
-      const Plan p = ens_plan_for(n_act, nb, P.exact);
+      const Plan p = ens_plan_for(n_act, nb, P.exact, per_item);
       E.plan[c] = p;
       items = n_act ? p.n_g * p.S : 0;
       parts = n_act ? 5LL * p.S * n_act : 0;
-      if (n_act)
-        atomicAdd(&s_inter, (unsigned long long)n_act * (unsigned long long)nb);
     }
     const int ci = c_items, cn = c_nact;
     const long long cp = c_part;
@@ -237,6 +293,7 @@ __global__ void __launch_bounds__(kPlanThreads)
     E.part_off[E.nc] = c_part;
     E.totals[0] = c_items;
     E.totals[1] = c_nact;
+    E.totals[4] = 0;  // the force launch's item counter
     if (!init) {
       E.totals[3] = (int)ctl->slot[0].nrec;
       ctl->slot[0].nrec += c_nact;
@@ -261,6 +318,15 @@ __device__ __forceinline__ int find_cluster(const int* s_off, int nc, int w) {
       hi = mid - 1;
   }
   return lo;
+}
+
+// the block's next work item: one atomic per item on a counter the planner
+// zeroes (items below gridDim.x are taken statically by their blocks)
+__device__ __forceinline__ int next_item(const Ens& E, int& s_next) {
+  __syncthreads();  // the previous item's shared-memory use is over
+  if (threadIdx.x == 0) s_next = gridDim.x + atomicAdd(&E.totals[4], 1);
+  __syncthreads();
+  return s_next;
 }
 
 __device__ __forceinline__ ForceArgs cluster_args(const Bodies& B,
@@ -298,7 +364,10 @@ __global__ void __launch_bounds__(kThreads, kMixMinBlocks)
   __shared__ float red[9][kThreads];
   for (int c = threadIdx.x; c <= E.nc; c += blockDim.x) s_off[c] = E.item_off[c];
   __syncthreads();
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+  __shared__ int s_next;
+  // items of different clusters differ in cost: after its first item a
+  // block takes the next free one from a counter (dynamic balance)
+  for (int w = blockIdx.x; w < total; w = next_item(E, s_next)) {
     const int c = find_cluster(s_off, E.nc, w);
     const Plan p = E.plan[c];
     const int local = w - s_off[c];
@@ -334,7 +403,10 @@ __global__ void __launch_bounds__(kThreads)
   __shared__ double red[5][kThreads];
   for (int c = threadIdx.x; c <= E.nc; c += blockDim.x) s_off[c] = E.item_off[c];
   __syncthreads();
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+  __shared__ int s_next;
+  // items of different clusters differ in cost: after its first item a
+  // block takes the next free one from a counter (dynamic balance)
+  for (int w = blockIdx.x; w < total; w = next_item(E, s_next)) {
     const int c = find_cluster(s_off, E.nc, w);
     const Plan p = E.plan[c];
     const int local = w - s_off[c];

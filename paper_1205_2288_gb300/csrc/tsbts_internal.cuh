@@ -149,7 +149,9 @@ struct Ens {
   int* act_base;         // nc + 1: prefix of active counts
   long long* part_off;   // nc + 1: prefix of partial sums (doubles)
   int* totals;           // [0] items, [1] active bodies, [2] clusters
-                         // still stepping, [3] record base of this step
+                         // still stepping, [3] record base of this step,
+                         // [4] items taken by the force launch
+  long long part_cap;    // doubles in the partial-sum buffer
 };
 
 // Work plan of one force launch: IG active bodies per work item (128 / IG
