@@ -438,6 +438,12 @@ def force_sweep(args):
             for _ in range(args.warmup if prec == tsbts.TSBTS_MIXED else 1):
                 tsbts.tsbts_force(prec, dm, dr, dv, eps, idx, a, phi, q)
             torch.cuda.synchronize()
+            if args.profile_range:
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
+                tsbts.tsbts_force(prec, dm, dr, dv, eps, idx, a, phi, q)
+                torch.cuda.synchronize()
+                torch.cuda.profiler.stop()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -720,9 +726,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=0,
                     help="--adjoint: use the schedule's first N steps")
     ap.add_argument("--profile-range", action="store_true",
-                    help="--adjoint: bracket the first timed mixed gradient "
-                         "with cudaProfilerStart/Stop (for ncu "
-                         "--profile-from-start off)")
+                    help="bracket the first timed step (--adjoint: the "
+                         "first timed mixed gradient) with cudaProfilerStart/"
+                         "Stop (for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.force_sweep:
         return force_sweep(args)
@@ -783,14 +789,19 @@ def main():
         barrier(dist)
         torch.cuda.synchronize()
         sampler.start()
-        for _ in range(args.steps):
+        for k in range(args.steps):
             flush.fill_(1)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
+            if args.profile_range and k == 0:
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
             ev0.record(stream)
             st = one_step(TIMING_PERIOD)
             ev1.record(stream)
             ev1.synchronize()
+            if args.profile_range and k == 0:
+                torch.cuda.profiler.stop()
             elapsed_ms += ev0.elapsed_time(ev1)
             tot_inter += st["interactions"]
             tot_steps += st["block_steps"]
