@@ -54,6 +54,11 @@ SM_COUNT = 152              # GB300; replaced by the device's own count
 FP32_LANES_PER_SM = 128
 NOMINAL_SM_MHZ = 2070.0
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_plummer16384_t1.json")
+# DRAM bytes (read + write) per force launch from one ncu capture of this
+# workload's first 2^-7 time units (cold cache, 1153 launches averaged);
+# the algorithmic bytes of a launch are the j records, n x 48 B
+FORCE_TRAFFIC_BYTES = 861313
+FORCE_ALGORITHMIC_BYTES = N_BODIES * 48
 METRIC = ("G pair-interactions/s, mixed vs FP64 on same GB300 at "
           "|dE/E|<=2x oracle; steps/s")
 WORKLOAD = "plummer16384_eps1-256_eta0.01_dynamic_era_3iter_t0-1"
@@ -848,7 +853,11 @@ def main():
         achieved = force_inter / (force_ms / 1e3) if force_ms > 0 else 0.0
         roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_g,
                 "unit": "Ginteractions/s", "frac": achieved / 1e9 / peak_g,
-                "traffic": None, "kernel": "force_mixed_kernel",
+                "traffic": FORCE_TRAFFIC_BYTES,
+                "traffic_unit": "DRAM bytes per force launch (ncu, cold "
+                                "cache; the live j set is L2-resident)",
+                "algorithmic_bytes_per_launch": FORCE_ALGORITHMIC_BYTES,
+                "kernel": "force_mixed_kernel",
                 "peak_basis": "FP32 FMA lane-ops/s measured on this GPU by "
                               "tsbts_pipe_peak / 20 FMA-pipe ops per "
                               "interaction",
