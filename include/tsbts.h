@@ -276,8 +276,10 @@ int tsbts_force_static(int precision, int exact_order, int64_t n,
  * The paper defines no adjoint; this is the reading taken here. The
  * gradient of a function of the bodies' final state with respect to their
  * initial positions, velocities and masses is taken through one era's
- * final-pass block schedule, replayed as plain block steps: every body is
- * predicted to the block time with Eq. 2 from its own time, the active
+ * final-pass block schedule (tsbts_adjoint_init), or through all its
+ * passes (tsbts_adjoint_init_era), replayed as plain block steps: every
+ * body is predicted to the block time (with Eq. 2 from its own time; in a
+ * later pass of an era from the previous pass's records), the active
  * bodies get the force sums of Eq. 3 at the predicted positions and are
  * corrected with Eq. 1 over their own step. The schedule (block times and
  * active sets) is held fixed and is not differentiated; the step criterion
@@ -304,6 +306,7 @@ typedef struct {
   double forward_ms;           /* device time of the last forward call */
   double backward_ms;          /* device time of the last reverse sweep */
   int64_t kernel_launches;     /* kernels launched by the adjoint */
+  int64_t passes;              /* passes of the era replayed */
 } tsbts_adjoint_stats;
 
 /* Set up the adjoint of a schedule over n bodies with softening eps >= 0.
@@ -324,6 +327,33 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps,
                        int64_t n_steps, const int64_t* step_tau,
                        const int64_t* step_off, const int32_t* act,
                        int64_t checkpoint_every);
+
+/* Adjoint through every pass of one era (Sec. 2, Alg. 2: each pass after
+ * the first places a body that is not active at a block time from the
+ * previous pass's records: the record itself on an exact hit, else the
+ * cubic Hermite between the two records that bracket the block time, else,
+ * past the body's last record, Eq. 2 from its own state). A body's records
+ * of a pass are its era-start state and its state after each of its steps
+ * in that pass.
+ *
+ * n_pass >= 1 passes; pass p is steps pass_off[p] .. pass_off[p+1] - 1
+ * (pass_off[0] = 0; with n_pass > 1 every pass has at least one step).
+ * step_tau, step_off and act hold every step of every pass in order, in
+ * the layout of tsbts_adjoint_init (step_off runs on across the passes);
+ * the ticks increase from > 0 within each pass, since each pass restarts
+ * from the era start at tick 0. The forward replay returns the last pass's
+ * final state; reverse mode differentiates through every pass, the
+ * cotangent of an interpolated position passing to the records it came
+ * from with the Hermite weights. Memory beyond tsbts_adjoint_init: 104
+ * bytes per entry of every pass but the last (records, their cotangents
+ * and ticks), 16 bytes per body per pass for the record bookkeeping, and
+ * a final state per pass when nothing is checkpointed; checkpointed
+ * segments (checkpoint_every) stay within one pass. n_pass = 1 is
+ * tsbts_adjoint_init. TSBTS_ERR_ARG: a bad size or schedule. */
+int tsbts_adjoint_init_era(tsbts_ctx* ctx, int64_t n, double eps,
+                           int64_t n_pass, const int64_t* pass_off,
+                           const int64_t* step_tau, const int64_t* step_off,
+                           const int32_t* act, int64_t checkpoint_every);
 
 /* Forward replay from masses m[n], positions r0[n*3] and velocities
  * v0[n*3] at tick 0 (initial accelerations: the force on every body at

@@ -22,15 +22,16 @@ import torch
 from . import tsbts
 
 
-def make_adjoint(n, eps, schedule, *, precision=tsbts.TSBTS_FP64, k_max=20,
-                 checkpoint_every=0, device=0):
-    """An Adjoint running on its own torch stream of `device`; every call
-    first waits for the caller's current stream, and returns once its
-    results are written."""
+def make_adjoint(n, eps, schedule=None, *, passes=None,
+                 precision=tsbts.TSBTS_FP64, k_max=20, checkpoint_every=0,
+                 device=0):
+    """An Adjoint (of one pass's schedule, or of every pass of an era) on
+    its own torch stream of `device`; every call first waits for the
+    caller's current stream, and returns once its results are written."""
     stream = torch.cuda.Stream(device=device)
-    adj = tsbts.Adjoint(n, eps, schedule, precision=precision, k_max=k_max,
-                        checkpoint_every=checkpoint_every, device=device,
-                        stream=stream.cuda_stream)
+    adj = tsbts.Adjoint(n, eps, schedule, passes=passes, precision=precision,
+                        k_max=k_max, checkpoint_every=checkpoint_every,
+                        device=device, stream=stream.cuda_stream)
     adj.torch_stream = stream
     adj.generation = 0
     return adj

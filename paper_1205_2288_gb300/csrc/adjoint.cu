@@ -10,6 +10,13 @@
 // schedule entries (all of them, or one checkpointed segment), and
 // full-state checkpoints every K steps. With checkpointing the reverse
 // sweep recomputes each segment's forward steps from its checkpoint.
+//
+// Several passes of one era are one schedule whose entries run on across
+// the passes (each body's entry links too); every pass restarts from the
+// era-start state. Every pass but the last also keeps its records (each
+// entry's post-step position and velocity) and their cotangents, which the
+// next pass's predictions and their reverse mode use; checkpointed
+// segments stay within one pass.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -33,7 +40,31 @@ struct AdjCtx {
   long long K = 0;  // checkpoint every K steps (0: tape everything)
   long long n_ckpt = 0;
   long long tape_cap = 0;
+  long long n_pass = 1;
   std::vector<long long> tau, off;
+  std::vector<long long> pass_off;  // first step of each pass, then S
+  // checkpointed segments [seg0, seg1) of pass seg_pass; ckpt_of[s]: the
+  // segment that starts at step s, else -1
+  std::vector<long long> seg0, seg1, seg_pass, ckpt_of;
+  // several passes: records of every pass but the last (E_rec entries),
+  // each body's first and last entry in those passes ((n_pass - 1) x n),
+  // the forward and reverse record cursors, the era-start cotangents of
+  // two consecutive passes (g0[p & 1]: r then v), their sum G0 over the
+  // passes, the era-start state and each pass's final state (taped mode)
+  long long E_rec = 0;
+  AdjRecs Rc{};
+  long long* q_first = nullptr;
+  long long* q_last = nullptr;
+  long long* qf = nullptr;
+  long long* qr = nullptr;
+  double* g0[2][6] = {};
+  double* g0_block = nullptr;
+  double* G0_block = nullptr;
+  double* grec_block = nullptr;
+  AdjCot G0{};
+  AdjState St0{};
+  std::vector<AdjState> fins;
+  std::vector<long long*> ckpt_qf;
   std::vector<Plan> plans;      // forward force plan per step
   std::vector<VjpShape> shapes; // reverse work split per step
   VjpShape shape_init{};
@@ -186,30 +217,65 @@ void choose_plans(tsbts_ctx* c, AdjCtx& A) {
                             A.n, A.fl.grid, A.part_cap);
 }
 
-// Replay steps [s0, s1) from the current state (bodies already predicted
-// to the block time of step s0); with a tape, record the pre-step state of
-// their entries. With save_ckpt, checkpoint k (state and forward cursor)
-// is saved before step k K.
+// The pass p seen by the kernels, with record cursor `cur` (forward or
+// reverse); all off for a lone pass.
+AdjPass pass_desc(const AdjCtx& A, long long p, long long* cur) {
+  AdjPass Q{};
+  if (A.n_pass == 1) return Q;
+  Q.write = Q.inject = p + 1 < A.n_pass;
+  Q.cur = cur;
+  if (p > 0) {
+    Q.on = 1;
+    Q.lo = A.off[A.pass_off[p - 1]];
+    Q.hi = A.off[A.pass_off[p]];
+    Q.first = A.q_first + (p - 1) * (long long)A.n;
+    for (int c = 0; c < 3; ++c) {
+      Q.g0r[c] = A.g0[(p - 1) & 1][c];
+      Q.g0v[c] = A.g0[(p - 1) & 1][3 + c];
+    }
+  }
+  return Q;
+}
+
+// Replay steps [s0, s1) of pass p from the current state (bodies already
+// predicted to the block time of step s0); with a tape, record the
+// pre-step state of their entries. With save_ckpt, the checkpoint of a
+// segment (state, entry and record cursors) is saved before its first step.
 void replay_steps(tsbts_ctx* c, AdjCtx& A, long long s0, long long s1,
-                  const AdjTape& tape, bool save_ckpt) {
+                  const AdjTape& tape, bool save_ckpt, long long p) {
+  const AdjPass Q = pass_desc(A, p, A.qf);
+  const size_t nb = sizeof(long long) * (size_t)A.n;
   for (long long s = s0; s < s1; ++s) {
-    if (save_ckpt && A.K > 0 && s % A.K == 0) {
-      copy_state(A.ckpt[s / A.K], A.St, A.n, c->s);
-      ck(cudaMemcpyAsync(A.ckpt_fwd[s / A.K], A.fwd_e,
-                         sizeof(long long) * (size_t)A.n,
+    if (save_ckpt && A.K > 0 && A.ckpt_of[s] >= 0) {
+      const long long g = A.ckpt_of[s];
+      copy_state(A.ckpt[g], A.St, A.n, c->s);
+      ck(cudaMemcpyAsync(A.ckpt_fwd[g], A.fwd_e, nb,
                          cudaMemcpyDeviceToDevice, c->s),
          "checkpoint copy");
+      if (A.n_pass > 1)
+        ck(cudaMemcpyAsync(A.ckpt_qf[g], A.qf, nb, cudaMemcpyDeviceToDevice,
+                           c->s),
+           "checkpoint copy");
     }
     const long long T = A.tau[s];
     const int na = (int)(A.off[s + 1] - A.off[s]);
     launch_step_force(c, A, A.act + A.off[s], na, A.plans[s], A.shapes[s].si);
+    const bool more = s + 1 < s1;
     launch_adj_correct_predict(A.n, na, T, A.off[s], A.off[s + 1],
-                               s + 1 < s1 ? A.tau[s + 1] : -1, A.inv_ticks,
-                               A.mixed, A.part, A.nsplit, fsum_of(A), A.St,
-                               A.P, tape, A.fwd_e, A.next_e, A.err, c->s);
+                               more ? A.tau[s + 1] : -1,
+                               more ? A.off[s + 2] : 0, A.inv_ticks, A.mixed,
+                               A.part, A.nsplit, fsum_of(A), A.St, A.P, tape,
+                               A.fwd_e, A.next_e, A.Rc, Q, A.err, c->s);
     A.launches += 2;
   }
   ck(cudaGetLastError(), "replay launches");
+}
+
+// prediction of every body to the block time of step s of pass p
+void predict_to(tsbts_ctx* c, AdjCtx& A, long long s, long long p) {
+  launch_adj_predict(A.n, A.tau[s], A.inv_ticks, A.mixed, A.St, A.P, A.fwd_e,
+                     A.off[s + 1], A.Rc, pass_desc(A, p, A.qf), c->s);
+  A.launches += 1;
 }
 
 AdjBackPrep start_of(const AdjCtx& A, long long s) {
@@ -237,9 +303,9 @@ AdjBackFin end_of(const AdjCtx& A, long long s) {
 }
 
 void back_step(tsbts_ctx* c, AdjCtx& A, const AdjBackFin& F,
-               const AdjBackPrep& R) {
+               const AdjBackPrep& R, const AdjPass& Q) {
   launch_adj_back_step(A.n, A.inv_ticks, A.mixed, F, R, A.St, A.Tp, A.cur_e,
-                       A.prev_e, A.C, A.P, A.O, A.err, c->s);
+                       A.prev_e, A.C, A.P, A.O, A.Rc, Q, A.err, c->s);
   A.launches += 1;
 }
 
@@ -255,16 +321,19 @@ void vjp_of(tsbts_ctx* c, AdjCtx& A, long long s) {
   A.launches += 1;
 }
 
-// Reverse steps s1 - 1 down to s0, whose tape is loaded; step s0 - 1 is
-// started too when it needs no tape (the initial force, s0 = 0).
-void reverse_steps(tsbts_ctx* c, AdjCtx& A, long long s1, long long s0) {
+// Reverse steps s1 - 1 down to s0 of pass p, whose tape is loaded; step
+// s0 - 1 is started too when it needs no tape (a lone pass's initial force,
+// s0 = 0).
+void reverse_steps(tsbts_ctx* c, AdjCtx& A, long long s1, long long s0,
+                   long long p) {
   const AdjBackFin none_f{};
   AdjBackPrep none_r{};
-  back_step(c, A, none_f, start_of(A, s1 - 1));
+  const AdjPass Q = pass_desc(A, p, A.qr);
+  back_step(c, A, none_f, start_of(A, s1 - 1), Q);
   for (long long s = s1 - 1; s >= s0; --s) {
     vjp_of(c, A, s);
-    back_step(c, A, end_of(A, s),
-              s > s0 || s0 == 0 ? start_of(A, s - 1) : none_r);
+    const bool before = s > s0 || (s0 == 0 && A.n_pass == 1);
+    back_step(c, A, end_of(A, s), before ? start_of(A, s - 1) : none_r, Q);
   }
   ck(cudaGetLastError(), "reverse launches");
 }
@@ -290,8 +359,21 @@ void enqueue_forward(tsbts_ctx* c, AdjCtx& A) {
                      cudaMemcpyDeviceToDevice, c->s),
      "copy entry cursors");
   A.launches += 3;
+  if (A.n_pass > 1) copy_state(A.St0, A.St, A.n, c->s);
   AdjTape none{};
-  replay_steps(c, A, 0, A.S, A.K == 0 ? A.Tp : none, true);
+  for (long long p = 0; p < A.n_pass; ++p) {
+    const long long s0 = A.pass_off[p], s1 = A.pass_off[p + 1];
+    if (p > 0) {
+      // every pass starts from the era-start state, its record cursors at
+      // the era-start records
+      copy_state(A.St, A.St0, A.n, c->s);
+      ck(cudaMemsetAsync(A.qf, 0xFF, sizeof(long long) * n, c->s),
+         "memset");
+      predict_to(c, A, s0, p);
+    }
+    replay_steps(c, A, s0, s1, A.K == 0 ? A.Tp : none, true, p);
+    if (A.K == 0 && p + 1 < A.n_pass) copy_state(A.fins[p], A.St, A.n, c->s);
+  }
   // the taped reverse sweep starts from the final state; keep it so that
   // every sweep of this forward replay can start there
   if (A.K == 0) copy_state(A.fin, A.St, A.n, c->s);
@@ -299,34 +381,63 @@ void enqueue_forward(tsbts_ctx* c, AdjCtx& A) {
 
 // All work of the reverse sweep, from the seeds already in A.C.
 void enqueue_backward(tsbts_ctx* c, AdjCtx& A) {
-  ck(cudaMemcpyAsync(A.cur_e, A.last_e, sizeof(long long) * (size_t)A.n,
-                     cudaMemcpyDeviceToDevice, c->s),
+  const size_t nb = sizeof(long long) * (size_t)A.n;
+  ck(cudaMemcpyAsync(A.cur_e, A.last_e, nb, cudaMemcpyDeviceToDevice, c->s),
      "copy entry cursors");
-  if (A.K == 0) {
-    copy_state(A.St, A.fin, A.n, c->s);
-    reverse_steps(c, A, A.S, 0);
-  } else {
-    for (long long g = A.n_ckpt - 1; g >= 0; --g) {
-      const long long s0 = g * A.K, s1 = std::min(A.S, s0 + A.K);
-      copy_state(A.St, A.ckpt[g], A.n, c->s);
-      ck(cudaMemcpyAsync(A.fwd_e, A.ckpt_fwd[g],
-                         sizeof(long long) * (size_t)A.n,
-                         cudaMemcpyDeviceToDevice, c->s),
-         "checkpoint copy");
-      launch_adj_predict(A.n, A.tau[s0], A.inv_ticks, A.mixed, A.St, A.P,
-                         c->s);
-      A.launches += 1;
-      AdjTape tape = A.Tp;
-      tape.base = A.off[s0];
-      replay_steps(c, A, s0, s1, tape, false);
-      A.Tp.base = tape.base;
-      reverse_steps(c, A, s1, s0);
-    }
-    A.Tp.base = 0;
+  const bool multi = A.n_pass > 1;
+  if (multi) {
+    ck(cudaMemsetAsync(A.G0_block, 0, sizeof(double) * 9 * (size_t)A.n, c->s),
+       "memset");
+    ck(cudaMemsetAsync(A.g0_block, 0, sizeof(double) * 12 * (size_t)A.n,
+                       c->s),
+       "memset");
+    ck(cudaMemsetAsync(A.grec_block, 0,
+                       sizeof(double) * 6 * (size_t)std::max(A.E_rec, 1LL),
+                       c->s),
+       "memset");
   }
-  // the initial force a0 = f(r0) (started by the last reverse step)
+  for (long long p = A.n_pass - 1; p >= 0; --p) {
+    const long long s0 = A.pass_off[p], s1 = A.pass_off[p + 1];
+    if (p > 0)
+      ck(cudaMemcpyAsync(A.qr, A.q_last + (p - 1) * (long long)A.n, nb,
+                         cudaMemcpyDeviceToDevice, c->s),
+         "copy record cursors");
+    if (A.K == 0) {
+      copy_state(A.St, p + 1 == A.n_pass ? A.fin : A.fins[p], A.n, c->s);
+      reverse_steps(c, A, s1, s0, p);
+    } else {
+      for (long long g = A.n_ckpt - 1; g >= 0; --g) {
+        if (A.seg_pass[g] != p) continue;
+        const long long t0 = A.seg0[g], t1 = A.seg1[g];
+        copy_state(A.St, A.ckpt[g], A.n, c->s);
+        ck(cudaMemcpyAsync(A.fwd_e, A.ckpt_fwd[g], nb,
+                           cudaMemcpyDeviceToDevice, c->s),
+           "checkpoint copy");
+        if (multi)
+          ck(cudaMemcpyAsync(A.qf, A.ckpt_qf[g], nb, cudaMemcpyDeviceToDevice,
+                             c->s),
+             "checkpoint copy");
+        predict_to(c, A, t0, p);
+        AdjTape tape = A.Tp;
+        tape.base = A.off[t0];
+        replay_steps(c, A, t0, t1, tape, false, p);
+        A.Tp.base = tape.base;
+        reverse_steps(c, A, t1, t0, p);
+      }
+      A.Tp.base = 0;
+    }
+    if (multi) {
+      launch_adj_pass_end(A.n, A.C, A.G0, A.g0[p & 1], A.g0[p & 1] + 3,
+                          p == 0, c->s);
+      A.launches += 1;
+    }
+  }
+  // the initial force a0 = f(r0) (a lone pass's last reverse step has
+  // started it)
+  const AdjPass lone{};
+  if (multi) back_step(c, A, AdjBackFin{}, start_of(A, -1), lone);
   vjp_of(c, A, -1);
-  back_step(c, A, end_of(A, -1), AdjBackPrep{});
+  back_step(c, A, end_of(A, -1), AdjBackPrep{}, lone);
   ck(cudaGetLastError(), "reverse launches");
 }
 
@@ -422,32 +533,107 @@ void stage_in(tsbts_ctx* c, AdjCtx& A, const double* m, const double* r,
      "copy v");
 }
 
+// Records of every pass but the last, and the bookkeeping of the passes
+// (several passes only).
+void setup_records(tsbts_ctx* ctx, AdjCtx& A, const int32_t* act) {
+  const int ni = A.n;
+  const long long nq = A.n_pass - 1;
+  A.E_rec = A.off[A.pass_off[nq]];
+  std::vector<long long> first((size_t)(nq * ni), LLONG_MAX),
+      last((size_t)(nq * ni), -1), tau((size_t)std::max(A.E_rec, 1LL), 0);
+  for (long long p = 0; p < nq; ++p)
+    for (long long s = A.pass_off[p]; s < A.pass_off[p + 1]; ++s)
+      for (long long e = A.off[s]; e < A.off[s + 1]; ++e) {
+        const long long k = p * ni + act[e];
+        if (first[k] == LLONG_MAX) first[k] = e;
+        last[k] = e;
+        tau[e] = A.tau[s];
+      }
+  const size_t er = (size_t)std::max(A.E_rec, 1LL);
+  A.q_first = adj_alloc<long long>(A, first.size());
+  A.q_last = adj_alloc<long long>(A, last.size());
+  long long* ent_tau = adj_alloc<long long>(A, er);
+  ck(cudaMemcpyAsync(A.q_first, first.data(), sizeof(long long) * first.size(),
+                     cudaMemcpyHostToDevice, ctx->s),
+     "copy schedule");
+  ck(cudaMemcpyAsync(A.q_last, last.data(), sizeof(long long) * last.size(),
+                     cudaMemcpyHostToDevice, ctx->s),
+     "copy schedule");
+  ck(cudaMemcpyAsync(ent_tau, tau.data(), sizeof(long long) * er,
+                     cudaMemcpyHostToDevice, ctx->s),
+     "copy schedule");
+  A.qf = adj_alloc<long long>(A, ni);
+  A.qr = adj_alloc<long long>(A, ni);
+  A.St0 = alloc_state(A, ni);
+  AdjRecs& R = A.Rc;
+  double* rv = adj_alloc<double>(A, 6 * er);
+  A.grec_block = adj_alloc<double>(A, 6 * er);
+  for (int c = 0; c < 3; ++c) {
+    R.r[c] = rv + c * er;
+    R.v[c] = rv + (3 + c) * er;
+    R.gr[c] = A.grec_block + c * er;
+    R.gv[c] = A.grec_block + (3 + c) * er;
+    R.r0[c] = A.St0.r[c];
+    R.v0[c] = A.St0.v[c];
+  }
+  R.tau = ent_tau;
+  R.next_e = A.next_e;
+  R.prev_e = A.prev_e;
+  R.kind = adj_alloc<int>(A, ni);
+  R.ra = adj_alloc<long long>(A, ni);
+  R.rb = adj_alloc<long long>(A, ni);
+  A.g0_block = adj_alloc<double>(A, 12 * (size_t)ni);
+  for (int k = 0; k < 2; ++k)
+    for (int c = 0; c < 6; ++c) A.g0[k][c] = A.g0_block + (6 * k + c) * (size_t)ni;
+  A.G0_block = adj_alloc<double>(A, 9 * (size_t)ni);
+  for (int c = 0; c < 3; ++c) {
+    A.G0.gr[c] = A.G0_block + c * (size_t)ni;
+    A.G0.gv[c] = A.G0_block + (3 + c) * (size_t)ni;
+    A.G0.ga[c] = A.G0_block + (6 + c) * (size_t)ni;
+  }
+}
+
 }  // namespace
 
 void adjoint_release(tsbts_ctx* c) { adj_free(c); }
 
-extern "C" {
+namespace {
 
-int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
-                       const int64_t* step_tau, const int64_t* step_off,
-                       const int32_t* act, int64_t checkpoint_every) {
+// Set-up of the adjoint of n_pass passes (pass p: steps pass_off[p] ..
+// pass_off[p + 1]) of one schedule (tsbts_adjoint_init_era).
+int adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_pass,
+                 const int64_t* pass_off, const int64_t* step_tau,
+                 const int64_t* step_off, const int32_t* act,
+                 int64_t checkpoint_every) {
   if (!ctx) return TSBTS_ERR_ARG;
   if (ctx->poisoned) return fail(ctx, TSBTS_ERR_STATE, "context is poisoned");
   if (n < 1 || n > (1LL << 24))
     return fail(ctx, TSBTS_ERR_ARG, "n must be in [1, 2^24]");
   if (!(eps >= 0.0) || !std::isfinite(eps))
     return fail(ctx, TSBTS_ERR_ARG, "eps must be finite and >= 0");
-  if (n_steps < 0 || checkpoint_every < 0)
-    return fail(ctx, TSBTS_ERR_ARG, "negative step or checkpoint count");
+  if (n_pass < 1 || !pass_off)
+    return fail(ctx, TSBTS_ERR_ARG, "n_pass must be >= 1 with pass offsets");
+  if (pass_off[0] != 0)
+    return fail(ctx, TSBTS_ERR_ARG, "pass_off[0] must be 0");
+  for (int64_t p = 0; p < n_pass; ++p)
+    if (pass_off[p + 1] < pass_off[p] + (n_pass > 1 ? 1 : 0))
+      return fail(ctx, TSBTS_ERR_ARG,
+                  n_pass > 1 ? "every pass needs at least one step"
+                             : "negative step count");
+  const int64_t n_steps = pass_off[n_pass];
+  if (checkpoint_every < 0)
+    return fail(ctx, TSBTS_ERR_ARG, "negative checkpoint count");
   if (n_steps > 0 && (!step_tau || !step_off || !act))
     return fail(ctx, TSBTS_ERR_ARG, "null schedule array");
   if (n_steps > 0 && step_off[0] != 0)
     return fail(ctx, TSBTS_ERR_ARG, "step_off[0] must be 0");
   // validate the schedule: increasing ticks, non-empty steps, bodies in
   // range and distinct within a step
+  // (within each pass, which restarts at the era start)
   std::vector<long long> stamp((size_t)n, -1);
-  for (int64_t s = 0; s < n_steps; ++s) {
-    if (step_tau[s] <= (s ? step_tau[s - 1] : 0))
+  for (int64_t p = 0, s = 0; s < n_steps; ++s) {
+    while (s >= pass_off[p + 1]) ++p;
+    if (step_tau[s] <= (s > pass_off[p] ? step_tau[s - 1] : 0))
       return fail(ctx, TSBTS_ERR_ARG, "block ticks must increase from > 0");
     if (step_tau[s] > (1LL << 62))
       return fail(ctx, TSBTS_ERR_ARG, "block tick out of range");
@@ -480,6 +666,8 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     A.S = n_steps;
     A.E = E;
     A.K = checkpoint_every >= n_steps ? 0 : checkpoint_every;
+    A.n_pass = n_pass;
+    A.pass_off.assign(pass_off, pass_off + n_pass + 1);
     A.tau.assign(step_tau, step_tau + n_steps);
     A.off.assign(step_off, step_off + n_steps + 1);
     if (n_steps == 0) A.off.assign(1, 0);
@@ -555,16 +743,24 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     A.nsplit = adj_alloc<int>(A, 1);
     A.err = adj_alloc<int>(A, 1);
     A.loss = adj_alloc<double>(A, 2);
-    // tape: every entry, or the largest checkpointed segment
+    // tape: every entry, or the largest checkpointed segment (segments of
+    // K steps within each pass)
     const long long before_tape = A.bytes;
     if (A.K == 0) {
       A.tape_cap = E;
     } else {
-      A.n_ckpt = (A.S + A.K - 1) / A.K;
-      for (long long g = 0; g < A.n_ckpt; ++g) {
-        const long long s0 = g * A.K, s1 = std::min(A.S, s0 + A.K);
-        A.tape_cap = std::max(A.tape_cap, A.off[s1] - A.off[s0]);
-      }
+      A.ckpt_of.assign((size_t)A.S, -1);
+      for (long long p = 0; p < A.n_pass; ++p)
+        for (long long s0 = A.pass_off[p]; s0 < A.pass_off[p + 1];
+             s0 += A.K) {
+          const long long s1 = std::min(A.pass_off[p + 1], s0 + A.K);
+          A.ckpt_of[s0] = (long long)A.seg0.size();
+          A.seg0.push_back(s0);
+          A.seg1.push_back(s1);
+          A.seg_pass.push_back(p);
+          A.tape_cap = std::max(A.tape_cap, A.off[s1] - A.off[s0]);
+        }
+      A.n_ckpt = (long long)A.seg0.size();
     }
     for (int k = 0; k < 9; ++k) A.Tp.x[k] = adj_alloc<double>(A, A.tape_cap);
     A.Tp.tau = adj_alloc<long long>(A, A.tape_cap);
@@ -574,9 +770,15 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
     for (long long g = 0; g < A.n_ckpt; ++g) {
       A.ckpt.push_back(alloc_state(A, ni));
       A.ckpt_fwd.push_back(adj_alloc<long long>(A, ni));
+      if (A.n_pass > 1) A.ckpt_qf.push_back(adj_alloc<long long>(A, ni));
     }
-    if (A.K == 0) A.fin = alloc_state(A, ni);
+    if (A.K == 0) {
+      A.fin = alloc_state(A, ni);
+      for (long long p = 0; p + 1 < A.n_pass; ++p)
+        A.fins.push_back(alloc_state(A, ni));
+    }
     A.ckpt_bytes = A.bytes - before_ckpt;
+    if (A.n_pass > 1) setup_records(ctx, A, act);
     // reverse work splits and their partial-sum buffers
     A.shapes.resize(A.S);
     A.plans.resize(A.S);
@@ -612,6 +814,28 @@ int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
   } catch (const std::bad_alloc&) {
     return fail(ctx, TSBTS_ERR_CUDA, "host out of memory");
   }
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsbts_adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_steps,
+                       const int64_t* step_tau, const int64_t* step_off,
+                       const int32_t* act, int64_t checkpoint_every) {
+  if (ctx && n_steps < 0)
+    return fail(ctx, TSBTS_ERR_ARG, "negative step or checkpoint count");
+  const int64_t pass_off[2] = {0, n_steps};
+  return adjoint_init(ctx, n, eps, 1, pass_off, step_tau, step_off, act,
+                      checkpoint_every);
+}
+
+int tsbts_adjoint_init_era(tsbts_ctx* ctx, int64_t n, double eps,
+                           int64_t n_pass, const int64_t* pass_off,
+                           const int64_t* step_tau, const int64_t* step_off,
+                           const int32_t* act, int64_t checkpoint_every) {
+  return adjoint_init(ctx, n, eps, n_pass, pass_off, step_tau, step_off, act,
+                      checkpoint_every);
 }
 
 int tsbts_adjoint_forward(tsbts_ctx* ctx, const double* m, const double* r0,
@@ -726,6 +950,7 @@ int tsbts_adjoint_get_stats(tsbts_ctx* ctx, tsbts_adjoint_stats* out) {
   out->forward_ms = A.fwd_ms;
   out->backward_ms = A.bwd_ms;
   out->kernel_launches = A.launches;
+  out->passes = A.n_pass;
   return TSBTS_OK;
 }
 

@@ -1,7 +1,11 @@
 // Kernels of the adjoint of a frozen block schedule: the replay of an era's
-// final-pass schedule as plain block steps (Eq. 2 prediction of every body,
-// Eq. 3 force sums on the active bodies, Eq. 1 correction) and its reverse
-// mode, one block step at a time in reverse order.
+// passes as plain block steps (prediction of every body, Eq. 3 force sums
+// on the active bodies, Eq. 1 correction) and its reverse mode, one block
+// step at a time in reverse order. In the first pass (or a lone pass) every
+// body is predicted with Eq. 2 from its own state; in a later pass a body
+// that is not active is placed from the previous pass's records (Sec. 2:
+// the record on an exact hit, the cubic Hermite between the records that
+// bracket the block time, else Eq. 2).
 //
 // Reverse step at block time T with active set A, given the cotangents
 // (gr, gv, ga) of the post-step state:
@@ -19,6 +23,13 @@
 // The pre-step state of each active body is restored from the tape written
 // by the forward replay (or by the recomputation of a checkpointed
 // segment), so no arithmetic is run backwards.
+//
+// Through several passes: a position cotangent of a body placed from
+// records goes to those records (Hermite weights h00 and h10 h on record
+// A's r and v, h01 and h11 h on record B's); when the step that wrote a
+// record is reversed, the record's cotangent joins that of the body's
+// post-step state. Every pass starts from the era-start state, so the
+// passes' era-start cotangents add up (adj_pass_end_kernel).
 //
 // The FP64 replay uses the integrator's op-by-op FP64 expressions and force
 // kernels, so it reproduces a sequential FP64 replay bit for bit when the
@@ -95,6 +106,81 @@ __device__ __forceinline__ void predict_into(int j, long long T,
     P.jhi[j] = hi;
     P.jlo[j] = lo;
   }
+}
+
+// packed j records of a predicted position
+__device__ __forceinline__ void store_pred(int j, const double p[3], float w,
+                                           int mixed, const AdjPred& P) {
+  for (int c = 0; c < 3; ++c) P.p[c][j] = p[c];
+  if (mixed) {
+    float4 hi, lo;
+    pack_ds(p[0], p[1], p[2], w, hi, lo);
+    P.jhi[j] = hi;
+    P.jlo[j] = lo;
+  }
+}
+
+// ---------------------------------------------------------------------
+// Records of the previous pass
+// ---------------------------------------------------------------------
+
+// Move body j's record cursor forward to its last record in Q at or before
+// tick T (block ticks increase within a pass); each step follows the entry
+// links to a later entry, below Q.hi, so the loop ends.
+__device__ __forceinline__ long long q_advance(const AdjRecs& R,
+                                               const AdjPass& Q, int j,
+                                               long long T) {
+  const long long c0 = Q.cur[j];
+  long long cur = c0;
+  for (;;) {
+    const long long nx = cur < 0 ? Q.first[j] : R.next_e[cur];
+    if (nx >= Q.hi || R.tau[nx] > T) break;
+    cur = nx;
+  }
+  if (cur != c0) Q.cur[j] = cur;
+  return cur;
+}
+
+// The same cursor moved backward (the reverse sweep's ticks decrease);
+// each step follows the links to an earlier entry, or to -1 below Q.lo.
+__device__ __forceinline__ long long q_retreat(const AdjRecs& R,
+                                               const AdjPass& Q, int j,
+                                               long long T) {
+  const long long c0 = Q.cur[j];
+  long long cur = c0;
+  while (cur >= 0 && R.tau[cur] > T) {
+    const long long pe = R.prev_e[cur];
+    cur = pe >= Q.lo ? pe : -1;
+  }
+  if (cur != c0) Q.cur[j] = cur;
+  return cur;
+}
+
+// Position of body j at tick T from Q's records, cur being its last record
+// at or before T: the record on an exact hit (kind 1), the cubic Hermite
+// between cur and the next record (kind 2), or nothing past the last
+// record (kind 0: the caller uses Eq. 2). ra, rb: the records used.
+__device__ __forceinline__ int q_place(const AdjRecs& R, const AdjPass& Q,
+                                       int j, long long cur, long long T,
+                                       double inv_ticks, double p[3],
+                                       long long& ra, long long& rb) {
+  ra = cur;
+  rb = -1;
+  const long long ta = cur < 0 ? 0 : R.tau[cur];
+  if (cur >= 0 && ta == T) {
+    for (int c = 0; c < 3; ++c) p[c] = R.r[c][cur];
+    return 1;
+  }
+  const long long nx = cur < 0 ? Q.first[j] : R.next_e[cur];
+  if (nx >= Q.hi) return 0;
+  rb = nx;
+  const HermiteW w = hermite_weights(ta, R.tau[nx], T, inv_ticks);
+  for (int c = 0; c < 3; ++c) {
+    const double ya = cur < 0 ? R.r0[c][j] : R.r[c][cur];
+    const double da = cur < 0 ? R.v0[c][j] : R.v[c][cur];
+    p[c] = hermite1(w, ya, da, R.r[c][nx], R.v[c][nx]);
+  }
+  return 2;
 }
 
 // ---------------------------------------------------------------------
@@ -179,10 +265,20 @@ __global__ void adj_init_accel_kernel(int n, const double* part,
 }
 
 __global__ void adj_predict_kernel(int n, long long T, double inv_ticks,
-                                   int mixed, AdjState St, AdjPred P) {
+                                   int mixed, AdjState St, AdjPred P,
+                                   const long long* fwd_e, long long e_hi,
+                                   AdjRecs R, AdjPass Q) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
     double p[3];
+    if (Q.on && fwd_e[j] >= e_hi) {
+      long long ra, rb;
+      const long long cur = q_advance(R, Q, j, T);
+      if (q_place(R, Q, j, cur, T, inv_ticks, p, ra, rb)) {
+        store_pred(j, p, mixed ? (float)P.m[j] : 0.f, mixed, P);
+        continue;
+      }
+    }
     predict_into(j, T, inv_ticks, mixed, St, P, p);
   }
 }
@@ -192,27 +288,16 @@ __global__ void adj_predict_kernel(int n, long long T, double inv_ticks,
 // reached through pointers the compiler must assume may alias), so that a
 // body waits for at most two dependent rounds of memory accesses.
 
-// packed j records of a predicted position
-__device__ __forceinline__ void store_pred(int j, const double p[3], float w,
-                                           int mixed, const AdjPred& P) {
-  for (int c = 0; c < 3; ++c) P.p[c][j] = p[c];
-  if (mixed) {
-    float4 hi, lo;
-    pack_ds(p[0], p[1], p[2], w, hi, lo);
-    P.jhi[j] = hi;
-    P.jlo[j] = lo;
-  }
-}
-
 // Per body: Eq. 1 if the body is active in the step [e_lo, e_hi) of the
 // schedule (fwd_e[j] is its next entry not yet replayed; the tape receives
 // its pre-step state), then Eq. 2 prediction to the next block time T_next
 // (< 0: none).
 __global__ void adj_correct_predict_kernel(
     int n, int n_act, long long T, long long e_lo, long long e_hi,
-    long long T_next, double inv_ticks, int mixed, const double* part,
-    const int* nsplit, FSum F, AdjState St, AdjPred P, AdjTape Tp,
-    long long* fwd_e, const long long* next_e, int* err) {
+    long long T_next, long long e_hi_next, double inv_ticks, int mixed,
+    const double* part, const int* nsplit, FSum F, AdjState St, AdjPred P,
+    AdjTape Tp, long long* fwd_e, const long long* next_e, AdjRecs R,
+    AdjPass Q, int* err) {
   const int S = F.f[0] ? 1 : *nsplit;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
@@ -260,13 +345,26 @@ __global__ void adj_correct_predict_kernel(
       tau = T;
       St.tau[j] = T;
       fwd_e[j] = ne;
+      if (Q.write)
+        for (int c = 0; c < 3; ++c) {
+          R.r[c][e] = r[c];
+          R.v[c][e] = v[c];
+        }
     }
     if (T_next >= 0) {
-      const double h = tick_h(T_next, tau, inv_ticks);
       double q[3];
-      for (int c = 0; c < 3; ++c) {
-        double vp;
-        taylor1(r[c], v[c], a[c], h, q[c], vp);
+      int kind = 0;
+      if (Q.on && (active ? ne : e) >= e_hi_next) {
+        long long ra, rb;
+        const long long cur = q_advance(R, Q, j, T_next);
+        kind = q_place(R, Q, j, cur, T_next, inv_ticks, q, ra, rb);
+      }
+      if (!kind) {
+        const double h = tick_h(T_next, tau, inv_ticks);
+        for (int c = 0; c < 3; ++c) {
+          double vp;
+          taylor1(r[c], v[c], a[c], h, q[c], vp);
+        }
       }
       store_pred(j, q, mf, mixed, P);
     }
@@ -295,7 +393,8 @@ __global__ void adj_back_step_kernel(int n, double inv_ticks, int mixed,
                                      AdjBackFin F, AdjBackPrep R, AdjState St,
                                      AdjTape Tp, long long* cur_e,
                                      const long long* prev_e, AdjCot C,
-                                     AdjPred P, VjpOut O, int* err) {
+                                     AdjPred P, VjpOut O, AdjRecs Rc,
+                                     AdjPass Q, int* err) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
     // first round of loads
@@ -362,24 +461,63 @@ __global__ void adj_back_step_kernel(int n, double inv_ticks, int mixed,
           !isfinite(G[3]))
         atomicOr(err, 1);
       gm += G[3];
-      const double h = tick_h(F.T, tau0, inv_ticks);
-      const double hh2 = 0.5 * h * h;
-      for (int c = 0; c < 3; ++c) {
-        gr[c] += gp[c];
-        gv[c] += h * gp[c];
-        ga[c] += hh2 * gp[c];
+      const int kind = kf < 0 && Q.on ? Rc.kind[j] : 0;
+      if (kind == 0) {
+        const double h = tick_h(F.T, tau0, inv_ticks);
+        const double hh2 = 0.5 * h * h;
+        for (int c = 0; c < 3; ++c) {
+          gr[c] += gp[c];
+          gv[c] += h * gp[c];
+          ga[c] += hh2 * gp[c];
+        }
+      } else {
+        // placed from the previous pass's records: their cotangents
+        const long long ra = Rc.ra[j];
+        double* ar[3];
+        for (int c = 0; c < 3; ++c) ar[c] = ra < 0 ? Q.g0r[c] + j : Rc.gr[c] + ra;
+        if (kind == 1) {
+          for (int c = 0; c < 3; ++c) *ar[c] += gp[c];
+        } else {
+          const long long rb = Rc.rb[j];
+          const long long ta = ra < 0 ? 0 : Rc.tau[ra];
+          const HermiteW w = hermite_weights(ta, Rc.tau[rb], F.T, inv_ticks);
+          for (int c = 0; c < 3; ++c) {
+            double* av = ra < 0 ? Q.g0v[c] + j : Rc.gv[c] + ra;
+            *ar[c] += w.h00 * gp[c];
+            *av += w.h10h * gp[c];
+            Rc.gr[c][rb] += w.h01 * gp[c];
+            Rc.gv[c][rb] += w.h11h * gp[c];
+          }
+        }
       }
       C.gm[j] = gm;
     }
+    // an active body's record cotangent (written when the next pass was
+    // reversed) joins its post-step state's
+    if (kr >= 0 && !R.all && Q.inject)
+      for (int c = 0; c < 3; ++c) {
+        gr[c] += Rc.gr[c][e];
+        gv[c] += Rc.gv[c][e];
+      }
     // start of the step at R.T
     if (R.active) {
       const AdjSlots& Sl = R.Sl;
       const double h = tick_h(R.T, tau1, inv_ticks);
       double p[3];
-      for (int c = 0; c < 3; ++c) {
-        double vp;
-        taylor1(r[c], v[c], a[c], h, p[c], vp);
+      int kind = 0;
+      if (kr < 0 && Q.on) {
+        long long ra, rb;
+        const long long cur = q_retreat(Rc, Q, j, R.T);
+        kind = q_place(Rc, Q, j, cur, R.T, inv_ticks, p, ra, rb);
+        Rc.kind[j] = kind;
+        Rc.ra[j] = ra;
+        Rc.rb[j] = rb;
       }
+      if (!kind)
+        for (int c = 0; c < 3; ++c) {
+          double vp;
+          taylor1(r[c], v[c], a[c], h, p[c], vp);
+        }
       if (kr >= 0 && !R.all) {
         for (int c = 0; c < 3; ++c) {
           St.r[c][j] = r[c];
@@ -417,6 +555,32 @@ __global__ void adj_back_step_kernel(int n, double inv_ticks, int mixed,
       C.gr[c][j] = gr[c];
       C.gv[c][j] = gv[c];
       C.ga[c][j] = ga[c];
+    }
+  }
+}
+
+// End of one pass's reverse sweep (every pass starts from the era-start
+// state): G0 += the state's cotangents plus those of the pass's era-start
+// records (cleared for the pass two earlier); the state's cotangents then
+// restart from zero for the pass before, or become G0 after the first pass.
+__global__ void adj_pass_end_kernel(int n, AdjCot C, AdjCot G0,
+                                    AdjPass Qp, int last) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += gridDim.x * blockDim.x) {
+    for (int c = 0; c < 3; ++c) {
+      const double sr = C.gr[c][j] + Qp.g0r[c][j];
+      const double sv = C.gv[c][j] + Qp.g0v[c][j];
+      const double r = G0.gr[c][j] + sr;
+      const double v = G0.gv[c][j] + sv;
+      const double a = G0.ga[c][j] + C.ga[c][j];
+      G0.gr[c][j] = r;
+      G0.gv[c][j] = v;
+      G0.ga[c][j] = a;
+      Qp.g0r[c][j] = 0.0;
+      Qp.g0v[c][j] = 0.0;
+      C.gr[c][j] = last ? r : 0.0;
+      C.gv[c][j] = last ? v : 0.0;
+      C.ga[c][j] = last ? a : 0.0;
     }
   }
 }
@@ -1107,23 +1271,26 @@ void launch_adj_init_accel(int n, const double* part, const int* nsplit,
 }
 
 void launch_adj_predict(int n, long long T, double inv_ticks, int mixed,
-                        const AdjState& St, const AdjPred& P, cudaStream_t s) {
-  adj_predict_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(n, T, inv_ticks,
-                                                           mixed, St, P);
+                        const AdjState& St, const AdjPred& P,
+                        const long long* fwd_e, long long e_hi,
+                        const AdjRecs& R, const AdjPass& Q, cudaStream_t s) {
+  adj_predict_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(
+      n, T, inv_ticks, mixed, St, P, fwd_e, e_hi, R, Q);
 }
 
 void launch_adj_correct_predict(int n, int n_act, long long T, long long e_lo,
                                 long long e_hi, long long T_next,
-                                double inv_ticks, int mixed,
-                                const double* part, const int* nsplit,
-                                double* const fsum[3], const AdjState& St,
-                                const AdjPred& P, const AdjTape& Tp,
-                                long long* fwd_e, const long long* next_e,
-                                int* err, cudaStream_t s) {
+                                long long e_hi_next, double inv_ticks,
+                                int mixed, const double* part,
+                                const int* nsplit, double* const fsum[3],
+                                const AdjState& St, const AdjPred& P,
+                                const AdjTape& Tp, long long* fwd_e,
+                                const long long* next_e, const AdjRecs& R,
+                                const AdjPass& Q, int* err, cudaStream_t s) {
   const FSum F{{fsum[0], fsum[1], fsum[2]}};
   adj_correct_predict_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(
-      n, n_act, T, e_lo, e_hi, T_next, inv_ticks, mixed, part, nsplit, F, St,
-      P, Tp, fwd_e, next_e, err);
+      n, n_act, T, e_lo, e_hi, T_next, e_hi_next, inv_ticks, mixed, part,
+      nsplit, F, St, P, Tp, fwd_e, next_e, R, Q, err);
 }
 
 void launch_adj_force(int n, int n_act, const int* idx, double eps2,
@@ -1146,9 +1313,22 @@ void launch_adj_back_step(int n, double inv_ticks, int mixed,
                           const AdjState& St, const AdjTape& Tp,
                           long long* cur_e, const long long* prev_e,
                           const AdjCot& C, const AdjPred& P, const VjpOut& O,
-                          int* err, cudaStream_t s) {
+                          const AdjRecs& Rc, const AdjPass& Q, int* err,
+                          cudaStream_t s) {
   adj_back_step_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(
-      n, inv_ticks, mixed, F, R, St, Tp, cur_e, prev_e, C, P, O, err);
+      n, inv_ticks, mixed, F, R, St, Tp, cur_e, prev_e, C, P, O, Rc, Q, err);
+}
+
+void launch_adj_pass_end(int n, const AdjCot& C, const AdjCot& G0,
+                         double* const g0r[3], double* const g0v[3], int last,
+                         cudaStream_t s) {
+  AdjPass Qp{};
+  for (int c = 0; c < 3; ++c) {
+    Qp.g0r[c] = g0r[c];
+    Qp.g0v[c] = g0v[c];
+  }
+  adj_pass_end_kernel<<<body_grid(n), kBodyThreads, 0, s>>>(n, C, G0, Qp,
+                                                            last);
 }
 
 void launch_adj_vjp(int mixed, int n, int n_act, const int* idx, double eps2,

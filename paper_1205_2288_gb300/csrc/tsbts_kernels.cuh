@@ -147,6 +147,43 @@ struct AdjBackPrep {
   long long e_lo;
   AdjSlots Sl;
 };
+// Records of an era's passes (adjoint through every pass, Sec. 2): the
+// position and velocity of each schedule entry's body after its step,
+// their cotangents, the block tick of every entry and the entry links. A
+// body's era-start state (r0, v0) is its record at tick 0 in every pass.
+// kind/ra/rb: how each body that is not active was placed at the step
+// being reversed (0: Eq. 2 from its own state; 1: record ra; 2: cubic
+// Hermite between records ra and rb; ra = -1 is the era-start record).
+struct AdjRecs {
+  double* r[3];
+  double* v[3];
+  double* gr[3];
+  double* gv[3];
+  const long long* tau;
+  const long long* next_e;
+  const long long* prev_e;
+  const double* r0[3];
+  const double* v0[3];
+  int* kind;
+  long long* ra;
+  long long* rb;
+};
+// The pass being replayed or reversed. on: it has a previous pass Q
+// (entries [lo, hi); first[j]: body j's first entry in Q, LLONG_MAX if
+// none), whose records place the bodies that are not active at a step;
+// cur[j]: body j's last record in Q at or before the current block tick
+// (-1: the era-start record); g0r/g0v: the cotangents of Q's era-start
+// records. write: the pass's entries write their records (a pass follows
+// it); inject: in reverse, an entry's record cotangent joins the
+// cotangent of the body's state after that step.
+struct AdjPass {
+  int on, write, inject;
+  long long lo, hi;
+  const long long* first;
+  long long* cur;
+  double* g0r[3];
+  double* g0v[3];
+};
 
 void launch_adj_load(int n, const double* m_in, const double* r_in,
                      const double* v_in, int mixed, double* m_out,
@@ -160,18 +197,25 @@ void launch_adj_init_accel(int n, const double* part, const int* nsplit,
                            double* const fsum[3], long long T_next,
                            double inv_ticks, int mixed, const AdjState& St,
                            const AdjPred& P, int* err, cudaStream_t s);
+// prediction of every body to tick T; in a pass with a previous pass (Q.on)
+// the bodies not active at T (fwd_e[j] >= e_hi) are placed from Q's records
 void launch_adj_predict(int n, long long T, double inv_ticks, int mixed,
-                        const AdjState& St, const AdjPred& P, cudaStream_t s);
+                        const AdjState& St, const AdjPred& P,
+                        const long long* fwd_e, long long e_hi,
+                        const AdjRecs& R, const AdjPass& Q, cudaStream_t s);
 // Eq. 1 for the bodies of schedule entries [e_lo, e_hi) (fwd_e: each
-// body's next entry), then the prediction of every body to T_next
+// body's next entry; their records written when Q.write), then the
+// prediction of every body to T_next (active there: entries below
+// e_hi_next)
 void launch_adj_correct_predict(int n, int n_act, long long T, long long e_lo,
                                 long long e_hi, long long T_next,
-                                double inv_ticks, int mixed,
-                                const double* part, const int* nsplit,
-                                double* const fsum[3], const AdjState& St,
-                                const AdjPred& P, const AdjTape& Tp,
-                                long long* fwd_e, const long long* next_e,
-                                int* err, cudaStream_t s);
+                                long long e_hi_next, double inv_ticks,
+                                int mixed, const double* part,
+                                const int* nsplit, double* const fsum[3],
+                                const AdjState& St, const AdjPred& P,
+                                const AdjTape& Tp, long long* fwd_e,
+                                const long long* next_e, const AdjRecs& R,
+                                const AdjPass& Q, int* err, cudaStream_t s);
 // mixed replay force on the active bodies idx[0..n_act) into O.f (the i
 // side's work split)
 void launch_adj_force(int n, int n_act, const int* idx, double eps2,
@@ -182,7 +226,14 @@ void launch_adj_back_step(int n, double inv_ticks, int mixed,
                           const AdjState& St, const AdjTape& Tp,
                           long long* cur_e, const long long* prev_e,
                           const AdjCot& C, const AdjPred& P, const VjpOut& O,
-                          int* err, cudaStream_t s);
+                          const AdjRecs& Rc, const AdjPass& Q, int* err,
+                          cudaStream_t s);
+// end of one pass's reverse sweep: G0 += the cotangents of the state (and
+// of the pass's era-start records g0r/g0v, which are then cleared); the
+// state's cotangents become G0 when `last` (the first pass) else zero
+void launch_adj_pass_end(int n, const AdjCot& C, const AdjCot& G0,
+                         double* const g0r[3], double* const g0v[3], int last,
+                         cudaStream_t s);
 void launch_adj_vjp(int mixed, int n, int n_act, const int* idx, double eps2,
                     const AdjPred& P, const AdjSlots& Sl, const VjpShape& V,
                     const VjpOut& O, cudaStream_t s);

@@ -44,7 +44,7 @@ EXPORTS = (
     "tsbts_init_ensemble", "tsbts_ensemble_energy", "tsbts_adjoint_init",
     "tsbts_adjoint_forward", "tsbts_adjoint_vjp", "tsbts_adjoint_loss_grad",
     "tsbts_adjoint_get_stats", "tsbts_step_estimates", "tsbts_set_state",
-    "tsbts_pipe_peak",
+    "tsbts_pipe_peak", "tsbts_adjoint_init_era",
 )
 
 
@@ -75,7 +75,8 @@ class tsbts_adjoint_stats(C.Structure):
                 ("tape_bytes", I64), ("checkpoint_bytes", I64),
                 ("device_bytes", I64), ("pairs_forward", I64),
                 ("pairs_backward", I64), ("forward_ms", C.c_double),
-                ("backward_ms", C.c_double), ("kernel_launches", I64)]
+                ("backward_ms", C.c_double), ("kernel_launches", I64),
+                ("passes", I64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -135,6 +136,8 @@ def lib():
         L.tsbts_release_scratch.argtypes = []
         L.tsbts_adjoint_init.argtypes = [VP, I64, C.c_double, I64, I64P,
                                          I64P, I32P, I64]
+        L.tsbts_adjoint_init_era.argtypes = [VP, I64, C.c_double, I64, I64P,
+                                             I64P, I64P, I32P, I64]
         L.tsbts_adjoint_forward.argtypes = [VP, VP, VP, VP, VP, VP, C.c_int]
         L.tsbts_adjoint_vjp.argtypes = [VP, VP, VP, VP, VP, VP, C.c_int]
         L.tsbts_adjoint_loss_grad.argtypes = [VP, VP, VP, VP, VP, VP, VP, VP,
@@ -379,6 +382,26 @@ def final_pass_schedule(sched, era=-1):
             step_off, act)
 
 
+def era_pass_schedules(sched, era=0):
+    """Every pass of one era from a schedule log (tsbts_schedule_get): a
+    list of (step_tau, step_off, act), one per pass in order, active bodies
+    ascending within each step."""
+    eras = np.unique(sched["era"])
+    in_era = sched["era"] == eras[era]
+    off = np.zeros(len(sched["n_act"]) + 1, np.int64)
+    np.cumsum(sched["n_act"], out=off[1:])
+    out = []
+    for p in np.unique(sched["pass_"][in_era]):
+        steps = np.flatnonzero(in_era & (sched["pass_"] == p))
+        parts = [np.sort(sched["idx"][off[k]:off[k + 1]]) for k in steps]
+        step_off = np.zeros(len(parts) + 1, np.int64)
+        np.cumsum([len(x) for x in parts], out=step_off[1:])
+        act = np.concatenate(parts).astype(np.int32)
+        out.append((np.ascontiguousarray(sched["tau"][steps], dtype=np.int64),
+                    step_off, act))
+    return out
+
+
 def tsbts_adjoint_init(ctx, n, eps, schedule, checkpoint_every=0):
     tau, off, act = (np.ascontiguousarray(schedule[0], np.int64),
                      np.ascontiguousarray(schedule[1], np.int64),
@@ -388,6 +411,39 @@ def tsbts_adjoint_init(ctx, n, eps, schedule, checkpoint_every=0):
     _check(lib().tsbts_adjoint_init(ctx, int(n), float(eps), tau.shape[0],
                                     _p(tau, I64P), _p(off, I64P),
                                     _p(act, I32P), int(checkpoint_every)), ctx)
+
+
+def era_schedule(passes):
+    """Concatenate per-pass schedules [(step_tau, step_off, act), ...] of
+    one era into (pass_off, step_tau, step_off, act) with step_off running
+    on across the passes."""
+    taus, offs, acts, pass_off, base = [], [], [], [0], 0
+    for tau, off, act in passes:
+        tau = np.asarray(tau, np.int64)
+        off = np.asarray(off, np.int64)
+        if off.shape[0] != tau.shape[0] + 1 or off[0] != 0:
+            raise ValueError("each pass needs step_off = [0, ...] with one "
+                             "more entry than step_tau")
+        taus.append(tau)
+        offs.append(off[:-1] + base)
+        acts.append(np.asarray(act, np.int32))
+        base += int(off[-1])
+        pass_off.append(pass_off[-1] + tau.shape[0])
+    offs.append(np.array([base], np.int64))
+    return (np.ascontiguousarray(pass_off, np.int64),
+            np.ascontiguousarray(np.concatenate(taus), np.int64),
+            np.ascontiguousarray(np.concatenate(offs), np.int64),
+            np.ascontiguousarray(np.concatenate(acts), np.int32))
+
+
+def tsbts_adjoint_init_era(ctx, n, eps, passes, checkpoint_every=0):
+    """Adjoint through every pass of one era; passes: one
+    (step_tau, step_off, act) per pass, in pass order."""
+    pass_off, tau, off, act = era_schedule(passes)
+    _check(lib().tsbts_adjoint_init_era(
+        ctx, int(n), float(eps), len(passes), _p(pass_off, I64P),
+        _p(tau, I64P), _p(off, I64P), _p(act, I32P), int(checkpoint_every)),
+        ctx)
 
 
 def _ptrs(arrays, n, device):
@@ -594,15 +650,19 @@ class Adjoint:
     """Adjoint of a frozen block schedule (tsbts_adjoint_*): replay of the
     schedule from (m, r0, v0) and reverse-mode gradients.
 
-    schedule = (step_tau, step_off, act) as from final_pass_schedule.
-    checkpoint_every = 0 tapes every step; K > 0 keeps a checkpoint every
-    K steps and recomputes during the reverse sweep. graph_steps = 0 runs
-    plain stream launches; otherwise the forward replay and the reverse
-    sweep are each captured once as a CUDA graph and replayed."""
+    schedule = (step_tau, step_off, act) as from final_pass_schedule, or
+    passes = a list of such schedules, every pass of one era (the adjoint
+    through all of them). checkpoint_every = 0 tapes every step; K > 0
+    keeps a checkpoint every K steps and recomputes during the reverse
+    sweep. graph_steps = 0 runs plain stream launches; otherwise the
+    forward replay and the reverse sweep are each captured once as a CUDA
+    graph and replayed."""
 
-    def __init__(self, n, eps, schedule, *, precision=TSBTS_FP64, k_max=20,
-                 checkpoint_every=0, exact_order=-1, device=0, stream=None,
-                 graph_steps=32):
+    def __init__(self, n, eps, schedule=None, *, passes=None,
+                 precision=TSBTS_FP64, k_max=20, checkpoint_every=0,
+                 exact_order=-1, device=0, stream=None, graph_steps=32):
+        if (schedule is None) == (passes is None):
+            raise ValueError("give either schedule or passes")
         cfg = tsbts_config_default()
         cfg.precision = precision
         cfg.k_max = k_max
@@ -613,7 +673,12 @@ class Adjoint:
         self.n = int(n)
         self.ctx = tsbts_create(cfg)
         try:
-            tsbts_adjoint_init(self.ctx, n, eps, schedule, checkpoint_every)
+            if passes is None:
+                tsbts_adjoint_init(self.ctx, n, eps, schedule,
+                                   checkpoint_every)
+            else:
+                tsbts_adjoint_init_era(self.ctx, n, eps, passes,
+                                       checkpoint_every)
         except Exception:
             tsbts_destroy(self.ctx)
             self.ctx = None
