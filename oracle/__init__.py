@@ -115,6 +115,13 @@ def lib():
             L.orc_era_replay_vjp.argtypes = [I64, DP, DP, DP, C.c_double,
                                              C.c_int, *era, DP, DP, DP, DP,
                                              DP]
+            L.orc_era_replay_state.argtypes = [I64, DP, DP, DP, DP, I64P,
+                                               C.c_double, C.c_int, *era,
+                                               DP, DP, DP, I64P]
+            L.orc_era_replay_state_vjp.argtypes = [I64, DP, DP, DP, DP, I64P,
+                                                   C.c_double, C.c_int, *era,
+                                                   DP, DP, DP, DP, DP, DP,
+                                                   DP]
             L.orc_loss_msr.argtypes = [I64, DP, DP, DP, DP]
             L.orc_loss_msr.restype = C.c_double
             _lib = L
@@ -314,6 +321,70 @@ def era_replay_vjp(m, r0, v0, eps, k_max, passes, gr_T, gv_T):
                              int(k_max), *ea, _p(gr_T), _p(gv_T), _p(g_r0),
                              _p(g_v0), _p(g_m))
     return g_r0, g_v0, g_m
+
+
+def _opt(x, t=DP):
+    return None if x is None else _p(x, t)
+
+
+def era_replay_state(m, r0, v0, a0, tau0, eps, k_max, passes):
+    """Multi-pass era replay from a general era-start state (each body at
+    tick tau0 with acceleration a0; None: tick 0 and the force at r0):
+    the last pass's final (r, v, a, tau)."""
+    m, r0, v0 = _d(m), _d(r0), _d(v0)
+    a0 = None if a0 is None else _d(a0)
+    tau0 = None if tau0 is None else np.ascontiguousarray(tau0, np.int64)
+    keep, ea = _era_args(passes)
+    r, v, a = np.zeros_like(r0), np.zeros_like(v0), np.zeros_like(r0)
+    tau = np.zeros(m.shape[0], np.int64)
+    lib().orc_era_replay_state(m.shape[0], _p(m), _p(r0), _p(v0), _opt(a0),
+                               _opt(tau0, I64P), float(eps), int(k_max), *ea,
+                               _p(r), _p(v), _p(a), _p(tau, I64P))
+    return r, v, a, tau
+
+
+def era_replay_state_vjp(m, r0, v0, a0, tau0, eps, k_max, passes, gr_T,
+                         gv_T, ga_T):
+    """Cotangents (g_r0, g_v0, g_a0, g_m) of era_replay_state for
+    cotangents of its final r, v, a (None: zero)."""
+    m, r0, v0 = _d(m), _d(r0), _d(v0)
+    a0 = None if a0 is None else _d(a0)
+    tau0 = None if tau0 is None else np.ascontiguousarray(tau0, np.int64)
+    gs = [None if g is None else _d(g) for g in (gr_T, gv_T, ga_T)]
+    keep, ea = _era_args(passes)
+    g_r0, g_v0, g_a0 = (np.zeros_like(r0) for _ in range(3))
+    g_m = np.zeros_like(m)
+    lib().orc_era_replay_state_vjp(m.shape[0], _p(m), _p(r0), _p(v0),
+                                   _opt(a0), _opt(tau0, I64P), float(eps),
+                                   int(k_max), *ea, *(_opt(g) for g in gs),
+                                   _p(g_r0), _p(g_v0), _p(g_a0), _p(g_m))
+    return g_r0, g_v0, g_a0, g_m
+
+
+def eras_replay(m, r0, v0, eps, k_max, eras):
+    """Replay of consecutive eras (each a list of passes) from (r0, v0) at
+    tick 0: every era starts from the state the era before it left. Returns
+    the final (r, v, a, tau) and the era-start states [(r, v, a, tau)]."""
+    state = (_d(r0), _d(v0), None, None)
+    starts = []
+    for passes in eras:
+        starts.append(state)
+        state = era_replay_state(m, *state, eps, k_max, passes)
+    return state, starts
+
+
+def eras_replay_vjp(m, r0, v0, eps, k_max, eras, gr_T, gv_T, ga_T=None):
+    """Adjoint across eras: the cotangents (g_r0, g_v0, g_m) of the
+    initial state for cotangents of the final r, v, a, chaining each era's
+    reverse mode from the last era to the first."""
+    _, starts = eras_replay(m, r0, v0, eps, k_max, eras)
+    g = (gr_T, gv_T, ga_T)
+    g_m = np.zeros(len(m))
+    for passes, st in zip(reversed(eras), reversed(starts)):
+        gr, gv, ga, gm = era_replay_state_vjp(m, *st, eps, k_max, passes, *g)
+        g_m += gm
+        g = (gr, gv, ga)
+    return g[0], g[1], g_m
 
 
 def loss_msr(m, r):

@@ -26,6 +26,14 @@
  * the era-start state). Every pass starts from the same era-start state,
  * so the passes' era-start cotangents add up; the initial force's
  * cotangent then goes through its vector-Jacobian product.
+ *
+ * Later eras: an era starts from the state the previous era left, each
+ * body at its own tick (a body whose step overshot the era end waits
+ * behind it, Sec. 3) with the acceleration of its last correction. The
+ * _state variants take that state (r0, v0, a0, tau0) as the input instead
+ * of (r0, v0) at tick 0 with a0 the force at r0, and return the cotangent
+ * of a0 instead of passing it through the initial force; chained era by
+ * era they give the adjoint across eras.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -64,7 +72,8 @@ typedef struct {
 } pass_t;
 
 static void pass_setup(pass_t* P, int64_t n, int64_t S, const int64_t* tau,
-                       const int64_t* off, const int32_t* act) {
+                       const int64_t* off, const int32_t* act,
+                       const int64_t* tau0) {
   P->S = S;
   P->E = S ? off[S] - off[0] : 0;
   P->tau = tau;
@@ -94,7 +103,8 @@ static void pass_setup(pass_t* P, int64_t n, int64_t S, const int64_t* tau,
       P->rec_tau[cnt[b]] = tau[s];
       cnt[b] += 1;
     }
-  for (int64_t b = 0; b < n; ++b) P->rec_tau[P->rec_off[b]] = 0;
+  for (int64_t b = 0; b < n; ++b)
+    P->rec_tau[P->rec_off[b]] = tau0 ? tau0[b] : 0;
   free(cnt);
 }
 
@@ -176,6 +186,7 @@ typedef struct {
   double *rp, *vp, *f, *phi, *q;
   int64_t* stamp;  /* per body: the step it was last active in */
   int64_t clock;   /* steps visited so far (forward and reverse) */
+  const int64_t* tau0;  /* era-start tick of each body (NULL: all 0) */
 } era_t;
 
 /* forward replay of pass P (previous pass Q or NULL) from the era start */
@@ -188,7 +199,7 @@ static void pass_forward(era_t* X, pass_t* P, const pass_t* Q,
   memcpy(X->v, v0, n3);
   memcpy(X->a, a0, n3);
   for (int64_t b = 0; b < n; ++b) {
-    X->tau[b] = 0;
+    X->tau[b] = X->tau0 ? X->tau0[b] : 0;
     const int64_t k = P->rec_off[b];
     memcpy(P->rec_r + 3 * k, r0 + 3 * b, sizeof(double) * 3);
     memcpy(P->rec_v + 3 * k, v0 + 3 * b, sizeof(double) * 3);
@@ -287,13 +298,19 @@ static void force_vjp(int64_t n, const double* m, const double* p,
   free(gi);
 }
 
+/* a0_in NULL: a0 is the force at r0 */
 static void era_forward(era_t* X, pass_t* passes, int64_t n_pass,
-                        const double* r0, const double* v0, double* a0) {
+                        const double* r0, const double* v0,
+                        const double* a0_in, double* a0) {
   const int64_t n = X->n;
-  int32_t* all = (int32_t*)zalloc(sizeof(int32_t) * (size_t)n);
-  for (int64_t i = 0; i < n; ++i) all[i] = (int32_t)i;
-  orc_forces(n, X->m, r0, v0, X->eps, n, all, a0, X->phi, X->q);
-  free(all);
+  if (a0_in) {
+    memcpy(a0, a0_in, sizeof(double) * 3 * (size_t)n);
+  } else {
+    int32_t* all = (int32_t*)zalloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) all[i] = (int32_t)i;
+    orc_forces(n, X->m, r0, v0, X->eps, n, all, a0, X->phi, X->q);
+    free(all);
+  }
   for (int64_t p = 0; p < n_pass; ++p)
     pass_forward(X, &passes[p], p ? &passes[p - 1] : NULL, r0, v0, a0);
 }
@@ -301,8 +318,9 @@ static void era_forward(era_t* X, pass_t* passes, int64_t n_pass,
 static void setup(era_t* X, int64_t n, const double* m, double eps, int k_max,
                   pass_t* passes, int64_t n_pass, const int64_t* pass_off,
                   const int64_t* step_tau, const int64_t* step_off,
-                  const int32_t* act) {
+                  const int32_t* act, const int64_t* tau0) {
   X->n = n;
+  X->tau0 = tau0;
   X->m = m;
   X->eps = eps;
   X->k_max = k_max;
@@ -320,7 +338,8 @@ static void setup(era_t* X, int64_t n, const double* m, double eps, int k_max,
   X->clock = 0;
   for (int64_t p = 0; p < n_pass; ++p) {
     const int64_t s0 = pass_off[p], s1 = pass_off[p + 1];
-    pass_setup(&passes[p], n, s1 - s0, step_tau + s0, step_off + s0, act);
+    pass_setup(&passes[p], n, s1 - s0, step_tau + s0, step_off + s0, act,
+               tau0);
   }
 }
 
@@ -330,38 +349,54 @@ static void teardown(era_t* X, pass_t* passes, int64_t n_pass) {
   for (int64_t p = 0; p < n_pass; ++p) pass_free(&passes[p]);
 }
 
-void orc_era_replay(int64_t n, const double* m, const double* r0,
-                    const double* v0, double eps, int k_max, int64_t n_pass,
-                    const int64_t* pass_off, const int64_t* step_tau,
-                    const int64_t* step_off, const int32_t* act,
-                    double* r_out, double* v_out) {
+void orc_era_replay_state(int64_t n, const double* m, const double* r0,
+                          const double* v0, const double* a0_in,
+                          const int64_t* tau0, double eps, int k_max,
+                          int64_t n_pass, const int64_t* pass_off,
+                          const int64_t* step_tau, const int64_t* step_off,
+                          const int32_t* act, double* r_out, double* v_out,
+                          double* a_out, int64_t* tau_out) {
   era_t X;
   pass_t* passes = (pass_t*)zalloc(sizeof(pass_t) * (size_t)n_pass);
   setup(&X, n, m, eps, k_max, passes, n_pass, pass_off, step_tau, step_off,
-        act);
+        act, tau0);
   double* a0 = (double*)zalloc(sizeof(double) * 3 * (size_t)n);
-  era_forward(&X, passes, n_pass, r0, v0, a0);
-  memcpy(r_out, X.r, sizeof(double) * 3 * (size_t)n);
-  memcpy(v_out, X.v, sizeof(double) * 3 * (size_t)n);
+  era_forward(&X, passes, n_pass, r0, v0, a0_in, a0);
+  if (r_out) memcpy(r_out, X.r, sizeof(double) * 3 * (size_t)n);
+  if (v_out) memcpy(v_out, X.v, sizeof(double) * 3 * (size_t)n);
+  if (a_out) memcpy(a_out, X.a, sizeof(double) * 3 * (size_t)n);
+  if (tau_out) memcpy(tau_out, X.tau, sizeof(int64_t) * (size_t)n);
   free(a0);
   teardown(&X, passes, n_pass);
   free(passes);
 }
 
-void orc_era_replay_vjp(int64_t n, const double* m, const double* r0,
-                        const double* v0, double eps, int k_max,
-                        int64_t n_pass, const int64_t* pass_off,
-                        const int64_t* step_tau, const int64_t* step_off,
-                        const int32_t* act, const double* gr_T,
-                        const double* gv_T, double* g_r0, double* g_v0,
-                        double* g_m) {
+void orc_era_replay(int64_t n, const double* m, const double* r0,
+                    const double* v0, double eps, int k_max, int64_t n_pass,
+                    const int64_t* pass_off, const int64_t* step_tau,
+                    const int64_t* step_off, const int32_t* act,
+                    double* r_out, double* v_out) {
+  orc_era_replay_state(n, m, r0, v0, NULL, NULL, eps, k_max, n_pass,
+                       pass_off, step_tau, step_off, act, r_out, v_out, NULL,
+                       NULL);
+}
+
+void orc_era_replay_state_vjp(int64_t n, const double* m, const double* r0,
+                              const double* v0, const double* a0_in,
+                              const int64_t* tau0, double eps, int k_max,
+                              int64_t n_pass, const int64_t* pass_off,
+                              const int64_t* step_tau,
+                              const int64_t* step_off, const int32_t* act,
+                              const double* gr_T, const double* gv_T,
+                              const double* ga_T, double* g_r0, double* g_v0,
+                              double* g_a0, double* g_m) {
   era_t X;
   pass_t* passes = (pass_t*)zalloc(sizeof(pass_t) * (size_t)n_pass);
   setup(&X, n, m, eps, k_max, passes, n_pass, pass_off, step_tau, step_off,
-        act);
+        act, tau0);
   const size_t n3 = sizeof(double) * 3 * (size_t)n;
   double* a0 = (double*)zalloc(n3);
-  era_forward(&X, passes, n_pass, r0, v0, a0);
+  era_forward(&X, passes, n_pass, r0, v0, a0_in, a0);
   const double eps2 = eps * eps;
   double* gR = (double*)zalloc(n3);
   double* gV = (double*)zalloc(n3);
@@ -383,14 +418,14 @@ void orc_era_replay_vjp(int64_t n, const double* m, const double* r0,
       memcpy(X.a + 3 * b, t + 6, sizeof(double) * 3);
       X.tau[b] = (int64_t)t[9];
     }
-    if (p == n_pass - 1) {
-      memcpy(gR, gr_T, n3);
-      memcpy(gV, gv_T, n3);
-    } else {
-      memset(gR, 0, n3);
-      memset(gV, 0, n3);
-    }
+    memset(gR, 0, n3);
+    memset(gV, 0, n3);
     memset(gA, 0, n3);
+    if (p == n_pass - 1) {
+      if (gr_T) memcpy(gR, gr_T, n3);
+      if (gv_T) memcpy(gV, gv_T, n3);
+      if (ga_T) memcpy(gA, ga_T, n3);
+    }
     for (int64_t s = P->S - 1; s >= 0; --s) {
       const int64_t T = P->tau[s];
       const int64_t e0 = P->off[s] - P->off[0];
@@ -471,18 +506,37 @@ void orc_era_replay_vjp(int64_t n, const double* m, const double* r0,
       }
     }
   }
-  /* the initial force a0 = f(r0) on every body */
-  int32_t* all = (int32_t*)zalloc(sizeof(int32_t) * (size_t)n);
-  for (int64_t i = 0; i < n; ++i) all[i] = (int32_t)i;
   memset(gp, 0, n3);
-  force_vjp(n, m, r0, eps2, n, all, G0a, gp, gm);
-  for (int64_t x = 0; x < 3 * n; ++x) {
-    g_r0[x] = G0r[x] + gp[x];
-    g_v0[x] = G0v[x];
+  if (a0_in) {
+    /* a0 is an input: its cotangent is returned */
+    if (g_a0) memcpy(g_a0, G0a, n3);
+  } else {
+    /* the initial force a0 = f(r0) on every body */
+    int32_t* all = (int32_t*)zalloc(sizeof(int32_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) all[i] = (int32_t)i;
+    force_vjp(n, m, r0, eps2, n, all, G0a, gp, gm);
+    free(all);
+    if (g_a0) memset(g_a0, 0, n3);
   }
-  memcpy(g_m, gm, sizeof(double) * (size_t)n);
-  free(all); free(a0); free(gR); free(gV); free(gA); free(gp); free(lam);
+  for (int64_t x = 0; x < 3 * n; ++x) {
+    if (g_r0) g_r0[x] = G0r[x] + gp[x];
+    if (g_v0) g_v0[x] = G0v[x];
+  }
+  if (g_m) memcpy(g_m, gm, sizeof(double) * (size_t)n);
+  free(a0); free(gR); free(gV); free(gA); free(gp); free(lam);
   free(G0r); free(G0v); free(G0a); free(gm);
   teardown(&X, passes, n_pass);
   free(passes);
+}
+
+void orc_era_replay_vjp(int64_t n, const double* m, const double* r0,
+                        const double* v0, double eps, int k_max,
+                        int64_t n_pass, const int64_t* pass_off,
+                        const int64_t* step_tau, const int64_t* step_off,
+                        const int32_t* act, const double* gr_T,
+                        const double* gv_T, double* g_r0, double* g_v0,
+                        double* g_m) {
+  orc_era_replay_state_vjp(n, m, r0, v0, NULL, NULL, eps, k_max, n_pass,
+                           pass_off, step_tau, step_off, act, gr_T, gv_T,
+                           NULL, g_r0, g_v0, NULL, g_m);
 }

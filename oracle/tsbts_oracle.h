@@ -182,6 +182,32 @@ void orc_era_replay_vjp(int64_t n, const double* m, const double* r0,
                         const double* gv_T, double* g_r0, double* g_v0,
                         double* g_m);
 
+/* The same era replay from a general era-start state: body j at tick
+ * tau0[j] (NULL: all 0) with acceleration a0[j] (NULL: the force at r0),
+ * as a later era starts from what the era before it left (Sec. 3: a body
+ * whose step overshot the era end waits behind it). The block ticks of
+ * every pass exceed every tau0. Outputs (each may be NULL) the last pass's
+ * final r, v, a and tick of every body. The _vjp variant takes cotangents
+ * of that final r, v, a (each may be NULL for zero) and returns those of
+ * r0, v0, m and a0 (g_a0: zero when a0 is NULL, its cotangent then going
+ * through the initial force). Chained era by era: the adjoint across eras. */
+void orc_era_replay_state(int64_t n, const double* m, const double* r0,
+                          const double* v0, const double* a0,
+                          const int64_t* tau0, double eps, int k_max,
+                          int64_t n_pass, const int64_t* pass_off,
+                          const int64_t* step_tau, const int64_t* step_off,
+                          const int32_t* act, double* r_out, double* v_out,
+                          double* a_out, int64_t* tau_out);
+void orc_era_replay_state_vjp(int64_t n, const double* m, const double* r0,
+                              const double* v0, const double* a0,
+                              const int64_t* tau0, double eps, int k_max,
+                              int64_t n_pass, const int64_t* pass_off,
+                              const int64_t* step_tau,
+                              const int64_t* step_off, const int32_t* act,
+                              const double* gr_T, const double* gv_T,
+                              const double* ga_T, double* g_r0, double* g_v0,
+                              double* g_a0, double* g_m);
+
 /* Mass-weighted mean-square radius about the origin,
  * L = sum_i m_i |r_i|^2 / sum_i m_i, with its partial derivatives with
  * respect to r (g_r) and m (g_m); either may be NULL. */

@@ -135,3 +135,147 @@ def test_earlier_passes_contribute(era_case):
                            c["passes"][-1], grT1, np.zeros_like(grT1))[0]
     diff = np.abs(g1 - c["gr"]).max() / np.abs(c["gr"]).max()
     assert 1e-6 < diff < 1e-2
+
+
+# ---------------------------------------------------------------------
+# Across eras: each era starts from the state the era before it left, a
+# body whose step overshot the era end waiting behind it (Sec. 3).
+# ---------------------------------------------------------------------
+
+def waiting_system():
+    """A Plummer sphere plus one far, slow body whose step (dt_max = 1/8)
+    overshoots every era of 1/16: it waits behind two era ends out of
+    three, so later eras start from bodies at different ticks."""
+    m = inputs.salpeter_masses(40, 13)
+    _, r, v = inputs.plummer(40, 14, masses=m)
+    m = np.append(m, 2e-3)
+    r = np.vstack([r, [30.0, -8.0, 4.0]])
+    v = np.vstack([v, [0.0, 0.03, 0.01]])
+    return m, r, v
+
+
+@pytest.mark.parametrize("era_mode", [0, 1])
+def test_eras_replay_is_the_integrator(era_mode):
+    m, r, v = waiting_system()
+    s = integrate(m, r, v, 0.5, eps=0.02, eta=0.05, dt_max=1 / 8,
+                  era_mode=era_mode, era_log2=4, n_iter=3)
+    sched = s.schedule()
+    n_eras = len(np.unique(sched["era"]))
+    assert n_eras >= 3
+    eras = [oracle.era_passes(sched, k) for k in range(n_eras)]
+    (rT, vT, aT, tauT), starts = oracle.eras_replay(m, r, v, 0.02, K_MAX,
+                                                    eras)
+    st = s.state()
+    np.testing.assert_array_equal(rT, st["r"])
+    np.testing.assert_array_equal(vT, st["v"])
+    np.testing.assert_array_equal(aT, st["a"])
+    np.testing.assert_array_equal(tauT, st["tau"])
+    # with fixed eras of 1/16 some era starts with the far body (step 1/8)
+    # behind the era's start tick (dynamic eras grow to its step)
+    if era_mode == 0:
+        first_ticks = [e[0][0][0] for e in eras[1:]]
+        assert any(t0[-1] < ft - (1 << 16)
+                   for (_, _, _, t0), ft in zip(starts[1:], first_ticks))
+
+
+@pytest.fixture(scope="module")
+def eras_case():
+    m, r, v = waiting_system()
+    s = integrate(m, r, v, 0.25, eps=0.02, eta=0.05, dt_max=1 / 8,
+                  era_mode=0, era_log2=4, n_iter=3)
+    sched = s.schedule()
+    eras = [oracle.era_passes(sched, k)
+            for k in range(len(np.unique(sched["era"])))]
+    (rT, _, _, _), starts = oracle.eras_replay(m, r, v, 0.02, K_MAX, eras)
+    L, grT, gmL = oracle.loss_msr(m, rT)
+    gr, gv, gm = oracle.eras_replay_vjp(m, r, v, 0.02, K_MAX, eras, grT,
+                                        np.zeros_like(grT))
+    return dict(m=m, r=r, v=v, eras=eras, starts=starts, rT=rT, gr=gr,
+                gv=gv, gm=gm + gmL)
+
+
+def eras_loss(c, m, r, v):
+    (rT, _, _, _), _ = oracle.eras_replay(m, r, v, 0.02, K_MAX, c["eras"])
+    return oracle.loss_msr(m, rT)[0]
+
+
+@pytest.mark.parametrize("which", ["r", "v", "m"])
+def test_eras_gradient_matches_central_differences(eras_case, which):
+    c = eras_case
+    g = c["g" + which]
+    rng = np.random.default_rng({"r": 15, "v": 16, "m": 17}[which])
+    # (the loss through several eras is strongly curved: h = 1e-5 leaves a
+    # truncation error of ~1e-7 relative, falling as h^2)
+    h = 1e-6
+    for _ in range(2):
+        d = rng.standard_normal(g.shape)
+        args = dict(m=c["m"], r=c["r"], v=c["v"])
+        p, q = dict(args), dict(args)
+        p[which] = args[which] + h * d
+        q[which] = args[which] - h * d
+        fd = (eras_loss(c, **p) - eras_loss(c, **q)) / (2 * h)
+        an = float((g * d).sum())
+        scale = np.linalg.norm(g) * np.linalg.norm(d)
+        assert abs(fd - an) <= 1e-8 * scale, (which, fd, an)
+
+
+def test_eras_difference_error_falls_as_h_squared(eras_case):
+    c = eras_case
+    d = np.random.default_rng(20).standard_normal(c["gr"].shape)
+    an = float((c["gr"] * d).sum())
+
+    def fd(h):
+        return (eras_loss(c, c["m"], c["r"] + h * d, c["v"])
+                - eras_loss(c, c["m"], c["r"] - h * d, c["v"])) / (2 * h)
+    e4 = abs(fd(1e-4) - an)
+    e5 = abs(fd(1e-5) - an)
+    assert e5 < e4 / 30, (e4, e5)
+
+
+def test_state_start_acceleration_cotangent(eras_case):
+    """The cotangent of an era's start accelerations (what the era before
+    it hands on) against central differences of that era's replay."""
+    c = eras_case
+    k = len(c["eras"]) - 1
+    r0, v0, a0, tau0 = c["starts"][k]
+    passes = c["eras"][k]
+    m = c["m"]
+
+    def L(a):
+        rT = oracle.era_replay_state(m, r0, v0, a, tau0, 0.02, K_MAX,
+                                     passes)[0]
+        return oracle.loss_msr(m, rT)[0]
+    rT = oracle.era_replay_state(m, r0, v0, a0, tau0, 0.02, K_MAX, passes)[0]
+    _, grT, _ = oracle.loss_msr(m, rT)
+    g = oracle.era_replay_state_vjp(m, r0, v0, a0, tau0, 0.02, K_MAX, passes,
+                                    grT, None, None)
+    ga = g[2]
+    assert np.abs(ga).max() > 0
+    d = np.random.default_rng(18).standard_normal(a0.shape)
+    h = 1e-6
+    fd = (L(a0 + h * d) - L(a0 - h * d)) / (2 * h)
+    an = float((ga * d).sum())
+    assert abs(fd - an) <= 1e-7 * np.linalg.norm(ga) * np.linalg.norm(d)
+
+
+def test_eras_translation_and_boost_invariance(eras_case):
+    c = eras_case
+    T = c["eras"][-1][-1][0][-1] * 2.0 ** -K_MAX
+    rcm2 = 2 * (c["m"][:, None] * c["rT"]).sum(0) / c["m"].sum()
+    np.testing.assert_allclose(c["gr"].sum(0), rcm2, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(c["gv"].sum(0), T * rcm2, rtol=1e-10,
+                               atol=1e-12)
+
+
+def test_one_era_chain_is_the_era_adjoint(eras_case):
+    c = eras_case
+    one = c["eras"][:1]
+    rng = np.random.default_rng(19)
+    gr_T = rng.standard_normal(c["r"].shape)
+    gv_T = rng.standard_normal(c["r"].shape)
+    a = oracle.eras_replay_vjp(c["m"], c["r"], c["v"], 0.02, K_MAX, one,
+                               gr_T, gv_T)
+    b = oracle.era_replay_vjp(c["m"], c["r"], c["v"], 0.02, K_MAX, one[0],
+                              gr_T, gv_T)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)

@@ -146,6 +146,21 @@ MUTANTS = [
     ('tsbts_adjoint_era.c', 'records_ignored_all', 'interpolated predictions treated as Taylor',
      '} else if (how[j].kind == 1) {',
      '} else if (0) {'),
+    ('tsbts_adjoint_era.c', 'start_record_tick_zero', 'later era: era-start records at tick 0',
+     'P->rec_tau[P->rec_off[b]] = tau0 ? tau0[b] : 0;',
+     'P->rec_tau[P->rec_off[b]] = 0;'),
+    ('tsbts_adjoint_era.c', 'state_tau_ignored', 'later era: every body restarts at tick 0',
+     'X->tau[b] = X->tau0 ? X->tau0[b] : 0;',
+     'X->tau[b] = 0;'),
+    ('tsbts_adjoint_era.c', 'state_a0_ignored', 'later era: start accelerations recomputed',
+     '  if (a0_in) {\n    memcpy(a0, a0_in,',
+     '  if (0) {\n    memcpy(a0, a0_in,'),
+    ('tsbts_adjoint_era.c', 'ga_T_dropped', 'across eras: final acceleration cotangent dropped',
+     'if (ga_T) memcpy(gA, ga_T, n3);',
+     ''),
+    ('tsbts_adjoint_era.c', 'g_a0_not_returned', 'across eras: start acceleration cotangent lost',
+     'if (g_a0) memcpy(g_a0, G0a, n3);',
+     'if (g_a0) memset(g_a0, 0, n3);'),
     # (the record-by-record time test alone is not reached in practice:
     # passes with equal record counts have had equal record times in every
     # case tried, so the mistake planted drops the whole schedule test)
