@@ -349,32 +349,41 @@ def config_results(local, stream, peak_g):
                            precision=tsbts.TSBTS_MIXED)
     sim.schedule_log(40_000_000)
     sim.step_era(t_era)
-    sched = tsbts.final_pass_schedule(sim.schedule(), 0)
+    log = sim.schedule()
     sim.close()
-    E = int(sched[1][-1])
-    adj = tsbts.Adjoint(n, eps, sched, precision=tsbts.TSBTS_MIXED,
-                        stream=stream.cuda_stream)
     dm, dr, dv = (torch.from_numpy(x).to(f"cuda:{local}") for x in (m, r, v))
     loss = torch.empty(1, dtype=torch.float64, device=dm.device)
     gr = [torch.empty((n, 3), dtype=torch.float64, device=dm.device),
           torch.empty((n, 3), dtype=torch.float64, device=dm.device),
           torch.empty((n,), dtype=torch.float64, device=dm.device)]
-    with torch.cuda.stream(stream):
-        tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *gr,
-                                      device=True)
-        e_a = torch.cuda.Event(enable_timing=True)
-        e_b = torch.cuda.Event(enable_timing=True)
-        e_a.record(stream)
-        tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *gr,
-                                      device=True)
-        e_b.record(stream)
-        e_b.synchronize()
-    ms = e_a.elapsed_time(e_b)
-    adj.close()
-    out["adjoint_plummer8192_era0-0.25"] = {
-        "ms_per_gradient": ms, "gradients_s": 1e3 / ms,
-        "Gpairs_s": 3 * (E + n) * n / (ms / 1e3) / 1e9,
-        "schedule_entries": E, "precision": "mixed, taped"}
+
+    def one_gradient(**which):
+        adj = tsbts.Adjoint(n, eps, precision=tsbts.TSBTS_MIXED,
+                            stream=stream.cuda_stream, **which)
+        with torch.cuda.stream(stream):
+            tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *gr,
+                                          device=True)
+            e_a = torch.cuda.Event(enable_timing=True)
+            e_b = torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            tsbts.tsbts_adjoint_loss_grad(adj.ctx, dm, dr, dv, loss, *gr,
+                                          device=True)
+            e_b.record(stream)
+            e_b.synchronize()
+        st = adj.stats()
+        adj.close()
+        ms = e_a.elapsed_time(e_b)
+        E = st["entries"]
+        return {"ms_per_gradient": ms, "gradients_s": 1e3 / ms,
+                "Gpairs_s": 3 * (E + n) * n / (ms / 1e3) / 1e9,
+                "schedule_entries": E, "passes": st["passes"],
+                "precision": "mixed, taped"}
+    # the final pass alone, and every pass of the era (the previous pass's
+    # records carry part of the gradient)
+    out["adjoint_plummer8192_era0-0.25"] = one_gradient(
+        schedule=tsbts.final_pass_schedule(log, 0))
+    out["adjoint_plummer8192_era0-0.25_all_passes"] = one_gradient(
+        passes=tsbts.era_pass_schedules(log, 0))
     return out
 
 

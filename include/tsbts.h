@@ -377,6 +377,35 @@ int tsbts_adjoint_vjp(tsbts_ctx* ctx, const double* gr_T, const double* gv_T,
                       double* g_r0, double* g_v0, double* g_m,
                       int device_ptrs);
 
+/* Forward replay from a general era-start state, for the adjoint across
+ * eras: a later era starts from the state the era before it left, each
+ * body at its own tick tau0[j] (a body whose step overshot the era end
+ * waits behind it, Sec. 3) with the acceleration a0[n*3] of its last
+ * correction. a0 = NULL (and tau0 = NULL) is tsbts_adjoint_forward: tick
+ * 0 and a0 the force at r0; tau0 = NULL with a0 given: every body at tick
+ * 0. Every tau0 must be >= 0 and below every pass's first block tick
+ * (TSBTS_ERR_ARG). Outputs the final r_T, v_T, a_T [n*3] and ticks
+ * tau_T[n] (each may be NULL), the input state of the next era. Pointers
+ * as in tsbts_adjoint_forward. */
+int tsbts_adjoint_forward_state(tsbts_ctx* ctx, const double* m,
+                                const double* r0, const double* v0,
+                                const double* a0, const int64_t* tau0,
+                                double* r_T, double* v_T, double* a_T,
+                                int64_t* tau_T, int device_ptrs);
+
+/* Reverse mode of the last forward replay with cotangents of the final
+ * r, v and a (each may be NULL for zero): writes the cotangents of r0, v0,
+ * a0 and m (each may be NULL). After a replay from a general start state
+ * g_a0 is the start accelerations' cotangent (and no initial force is
+ * differentiated); after one from tick 0 it is zero, a0 being the force
+ * at r0. Chaining this era by era, last to first, each era's (g_r0, g_v0,
+ * g_a0) being the previous era's (gr_T, gv_T, ga_T) and the g_m summed,
+ * differentiates across eras. TSBTS_ERR_STATE: no forward replay yet. */
+int tsbts_adjoint_vjp_state(tsbts_ctx* ctx, const double* gr_T,
+                            const double* gv_T, const double* ga_T,
+                            double* g_r0, double* g_v0, double* g_a0,
+                            double* g_m, int device_ptrs);
+
 /* Forward replay and reverse mode of the loss
  *   L = sum_i m_i |r_i(T)|^2 / sum_i m_i
  * (the mass-weighted mean-square radius about the origin of the final

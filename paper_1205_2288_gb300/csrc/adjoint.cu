@@ -82,7 +82,12 @@ struct AdjCtx {
   long long* fwd_e = nullptr;   // n: forward cursor
   int* iota = nullptr;          // n
   double* m = nullptr;
-  double* io = nullptr;         // 7 n doubles: host inputs / outputs
+  double* io = nullptr;         // 10 n doubles: host inputs / outputs
+  long long* tau_io = nullptr;  // n ticks: host start / final ticks
+  // the last forward replay started from a general state (r, v, a, tick)
+  // instead of (r, v) at tick 0 with the initial force
+  int state_mode = 0;
+  long long first_tick = LLONG_MAX;  // smallest first block tick of a pass
   AdjState St{};
   std::vector<AdjState> ckpt;
   std::vector<long long*> ckpt_fwd;  // forward cursor at each checkpoint
@@ -103,9 +108,10 @@ struct AdjCtx {
   long long pairs_fwd = 0, pairs_bwd = 0, launches = 0;
   double fwd_ms = 0, bwd_ms = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  // captured forward replay [0] and reverse sweep [1], and their kernels
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  long long graph_kernels[2] = {0, 0};
+  // captured forward replay [0] and reverse sweep [1], from tick 0 (+0) or
+  // from a general start state (+2), and their kernels
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long graph_kernels[4] = {0, 0, 0, 0};
 };
 
 }  // namespace tsbts
@@ -332,7 +338,9 @@ void reverse_steps(tsbts_ctx* c, AdjCtx& A, long long s1, long long s0,
   back_step(c, A, none_f, start_of(A, s1 - 1), Q);
   for (long long s = s1 - 1; s >= s0; --s) {
     vjp_of(c, A, s);
-    const bool before = s > s0 || (s0 == 0 && A.n_pass == 1);
+    // (a lone pass from tick 0: the initial force is started here)
+    const bool before =
+        s > s0 || (s0 == 0 && A.n_pass == 1 && !A.state_mode);
     back_step(c, A, end_of(A, s), before ? start_of(A, s - 1) : none_r, Q);
   }
   ck(cudaGetLastError(), "reverse launches");
@@ -346,19 +354,28 @@ void check_err(tsbts_ctx* c, AdjCtx& A, const char* what, int* rc) {
   if (e) *rc = fail(c, TSBTS_ERR_NONFINITE, what);
 }
 
-// All work of the forward replay, inputs read from A.io (m, r0, v0).
+// All work of the forward replay, inputs read from A.io (m, r0, v0, and in
+// state mode a0) and A.tau_io (state mode: tau0).
 void enqueue_forward(tsbts_ctx* c, AdjCtx& A) {
   const size_t n = (size_t)A.n;
-  launch_adj_load(A.n, A.io, A.io + n, A.io + 4 * n, A.mixed, A.m, A.St, A.P,
-                  A.err, c->s);
-  launch_step_force(c, A, A.iota, A.n, A.plan_init, A.shape_init.si);
-  launch_adj_init_accel(A.n, A.part, A.nsplit, fsum_of(A),
-                        A.S > 0 ? A.tau[0] : -1, A.inv_ticks, A.mixed, A.St,
-                        A.P, A.err, c->s);
+  const bool st = A.state_mode != 0;
+  launch_adj_load(A.n, A.io, A.io + n, A.io + 4 * n, st ? A.io + 7 * n : nullptr,
+                  st ? A.tau_io : nullptr, A.mixed, A.m, A.St, A.P, A.err,
+                  c->s);
   ck(cudaMemcpyAsync(A.fwd_e, A.first_e, sizeof(long long) * n,
                      cudaMemcpyDeviceToDevice, c->s),
      "copy entry cursors");
-  A.launches += 3;
+  A.launches += 1;
+  if (!st) {
+    // the initial force, then the prediction to the first block time
+    launch_step_force(c, A, A.iota, A.n, A.plan_init, A.shape_init.si);
+    launch_adj_init_accel(A.n, A.part, A.nsplit, fsum_of(A),
+                          A.S > 0 ? A.tau[0] : -1, A.inv_ticks, A.mixed,
+                          A.St, A.P, A.err, c->s);
+    A.launches += 2;
+  } else if (A.S > 0) {
+    predict_to(c, A, 0, 0);
+  }
   if (A.n_pass > 1) copy_state(A.St0, A.St, A.n, c->s);
   AdjTape none{};
   for (long long p = 0; p < A.n_pass; ++p) {
@@ -433,11 +450,14 @@ void enqueue_backward(tsbts_ctx* c, AdjCtx& A) {
     }
   }
   // the initial force a0 = f(r0) (a lone pass's last reverse step has
-  // started it)
-  const AdjPass lone{};
-  if (multi) back_step(c, A, AdjBackFin{}, start_of(A, -1), lone);
-  vjp_of(c, A, -1);
-  back_step(c, A, end_of(A, -1), AdjBackPrep{}, lone);
+  // started it); from a general start state the cotangents of (r0, v0, a0)
+  // are those of the state now
+  if (!A.state_mode) {
+    const AdjPass lone{};
+    if (multi) back_step(c, A, AdjBackFin{}, start_of(A, -1), lone);
+    vjp_of(c, A, -1);
+    back_step(c, A, end_of(A, -1), AdjBackPrep{}, lone);
+  }
   ck(cudaGetLastError(), "reverse launches");
 }
 
@@ -450,6 +470,7 @@ void run_work(tsbts_ctx* c, AdjCtx& A, int which,
     enq(c, A);
     return;
   }
+  which += 2 * A.state_mode;
   cudaGraphExec_t& exec = A.graph[which];
   if (!exec) {
     const long long l0 = A.launches;
@@ -519,10 +540,12 @@ void to_out(tsbts_ctx* c, AdjCtx& A, double* const src[3], double* dst,
   ck(cudaStreamSynchronize(c->s), "synchronize");
 }
 
-// inputs into A.io (m, r0, v0), from host or device arrays; the replay
-// always reads them there, so a captured graph serves every call
+// inputs into A.io (m, r0, v0, a0) and A.tau_io (tau0), from host or
+// device arrays; the replay always reads them there, so a captured graph
+// serves every call
 void stage_in(tsbts_ctx* c, AdjCtx& A, const double* m, const double* r,
-              const double* v, bool dev) {
+              const double* v, const double* a, const long long* tau,
+              bool dev) {
   const size_t n = (size_t)A.n;
   const cudaMemcpyKind kind =
       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -531,6 +554,14 @@ void stage_in(tsbts_ctx* c, AdjCtx& A, const double* m, const double* r,
      "copy r");
   ck(cudaMemcpyAsync(A.io + 4 * n, v, sizeof(double) * 3 * n, kind, c->s),
      "copy v");
+  if (a)
+    ck(cudaMemcpyAsync(A.io + 7 * n, a, sizeof(double) * 3 * n, kind, c->s),
+       "copy a");
+  if (a && tau)
+    ck(cudaMemcpyAsync(A.tau_io, tau, sizeof(long long) * n, kind, c->s),
+       "copy tau");
+  else if (a)
+    ck(cudaMemsetAsync(A.tau_io, 0, sizeof(long long) * n, c->s), "memset");
 }
 
 // Records of every pass but the last, and the bookkeeping of the passes
@@ -577,6 +608,7 @@ void setup_records(tsbts_ctx* ctx, AdjCtx& A, const int32_t* act) {
     R.v0[c] = A.St0.v[c];
   }
   R.tau = ent_tau;
+  R.tau0 = A.St0.tau;
   R.next_e = A.next_e;
   R.prev_e = A.prev_e;
   R.kind = adj_alloc<int>(A, ni);
@@ -710,7 +742,11 @@ int adjoint_init(tsbts_ctx* ctx, int64_t n, double eps, int64_t n_pass,
     ck(cudaMemcpyAsync(A.iota, iota.data(), sizeof(int) * ni,
                        cudaMemcpyHostToDevice, ctx->s), "copy iota");
     A.m = adj_alloc<double>(A, ni);
-    A.io = adj_alloc<double>(A, 7 * (size_t)ni);
+    A.io = adj_alloc<double>(A, 10 * (size_t)ni);
+    A.tau_io = adj_alloc<long long>(A, ni);
+    for (long long p = 0; p < n_pass; ++p)
+      if (A.pass_off[p + 1] > A.pass_off[p])
+        A.first_tick = std::min(A.first_tick, A.tau[A.pass_off[p]]);
     A.St = alloc_state(A, ni);
     for (int c = 0; c < 3; ++c) {
       A.P.p[c] = adj_alloc<double>(A, ni);
@@ -838,32 +874,73 @@ int tsbts_adjoint_init_era(tsbts_ctx* ctx, int64_t n, double eps,
                       checkpoint_every);
 }
 
-int tsbts_adjoint_forward(tsbts_ctx* ctx, const double* m, const double* r0,
-                          const double* v0, double* r_T, double* v_T,
-                          int device_ptrs) {
+int tsbts_adjoint_forward_state(tsbts_ctx* ctx, const double* m,
+                                const double* r0, const double* v0,
+                                const double* a0, const int64_t* tau0,
+                                double* r_T, double* v_T, double* a_T,
+                                int64_t* tau_T, int device_ptrs) {
   int rc = adj_ready(ctx);
   if (rc) return rc;
   if (!m || !r0 || !v0) return fail(ctx, TSBTS_ERR_ARG, "null input pointer");
+  if (tau0 && !a0)
+    return fail(ctx, TSBTS_ERR_ARG, "start ticks need start accelerations");
   AdjCtx& A = *ctx->adj;
   try {
     ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
-    stage_in(ctx, A, m, r0, v0, device_ptrs != 0);
+    const bool dev = device_ptrs != 0;
+    if (tau0) {
+      // every body's start tick must lie before every block tick
+      std::vector<long long> t((size_t)A.n);
+      if (dev) {
+        ck(cudaMemcpyAsync(t.data(), tau0, sizeof(long long) * (size_t)A.n,
+                           cudaMemcpyDeviceToHost, ctx->s),
+           "copy tau0");
+        ck(cudaStreamSynchronize(ctx->s), "synchronize");
+      } else {
+        std::memcpy(t.data(), tau0, sizeof(long long) * (size_t)A.n);
+      }
+      for (long long x : t)
+        if (x < 0 || x >= A.first_tick)
+          return fail(ctx, TSBTS_ERR_ARG,
+                      "start ticks must be >= 0 and before every block "
+                      "tick");
+    }
+    A.have_forward = false;
+    A.state_mode = a0 ? 1 : 0;
+    stage_in(ctx, A, m, r0, v0, a0, (const long long*)tau0, dev);
     rc = forward_impl(ctx, A);
     if (rc) return rc;
-    to_out(ctx, A, A.St.r, r_T, device_ptrs != 0);
-    to_out(ctx, A, A.St.v, v_T, device_ptrs != 0);
+    to_out(ctx, A, A.St.r, r_T, dev);
+    to_out(ctx, A, A.St.v, v_T, dev);
+    to_out(ctx, A, A.St.a, a_T, dev);
+    if (tau_T) {
+      ck(cudaMemcpyAsync(tau_T, A.St.tau, sizeof(long long) * (size_t)A.n,
+                         dev ? cudaMemcpyDeviceToDevice
+                             : cudaMemcpyDeviceToHost,
+                         ctx->s),
+         "copy tau");
+      ck(cudaStreamSynchronize(ctx->s), "synchronize");
+    }
     return TSBTS_OK;
   } catch (const CudaFail& f) {
     return cuda_fail(ctx, f);
   }
 }
 
+int tsbts_adjoint_forward(tsbts_ctx* ctx, const double* m, const double* r0,
+                          const double* v0, double* r_T, double* v_T,
+                          int device_ptrs) {
+  return tsbts_adjoint_forward_state(ctx, m, r0, v0, nullptr, nullptr, r_T,
+                                     v_T, nullptr, nullptr, device_ptrs);
+}
+
 namespace {
 
 int vjp_out(tsbts_ctx* ctx, AdjCtx& A, double* g_r0, double* g_v0,
-            double* g_m, bool dev) {
+            double* g_a0, double* g_m, bool dev) {
   to_out(ctx, A, A.C.gr, g_r0, dev);
   to_out(ctx, A, A.C.gv, g_v0, dev);
+  to_out(ctx, A, A.C.ga, g_a0, dev);
   if (g_m)
     ck(cudaMemcpyAsync(g_m, A.C.gm, sizeof(double) * A.n,
                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -875,9 +952,10 @@ int vjp_out(tsbts_ctx* ctx, AdjCtx& A, double* g_r0, double* g_v0,
 
 }  // namespace
 
-int tsbts_adjoint_vjp(tsbts_ctx* ctx, const double* gr_T, const double* gv_T,
-                      double* g_r0, double* g_v0, double* g_m,
-                      int device_ptrs) {
+int tsbts_adjoint_vjp_state(tsbts_ctx* ctx, const double* gr_T,
+                            const double* gv_T, const double* ga_T,
+                            double* g_r0, double* g_v0, double* g_a0,
+                            double* g_m, int device_ptrs) {
   int rc = adj_ready(ctx);
   if (rc) return rc;
   AdjCtx& A = *ctx->adj;
@@ -885,26 +963,34 @@ int tsbts_adjoint_vjp(tsbts_ctx* ctx, const double* gr_T, const double* gv_T,
     return fail(ctx, TSBTS_ERR_STATE, "tsbts_adjoint_forward not called");
   try {
     ck(cudaSetDevice(ctx->cfg.device), "cudaSetDevice");
-    const double *dgr = gr_T, *dgv = gv_T;
+    const double *dgr = gr_T, *dgv = gv_T, *dga = ga_T;
     const size_t n3 = 3 * (size_t)A.n;
     if (!device_ptrs) {
-      if (gr_T)
-        ck(cudaMemcpyAsync(A.io, gr_T, sizeof(double) * n3,
-                           cudaMemcpyHostToDevice, ctx->s), "copy gr");
-      if (gv_T)
-        ck(cudaMemcpyAsync(A.io + n3, gv_T, sizeof(double) * n3,
-                           cudaMemcpyHostToDevice, ctx->s), "copy gv");
-      dgr = gr_T ? A.io : nullptr;
-      dgv = gv_T ? A.io + n3 : nullptr;
+      const double* src[3] = {gr_T, gv_T, ga_T};
+      const double** dst[3] = {&dgr, &dgv, &dga};
+      for (int k = 0; k < 3; ++k) {
+        if (!src[k]) continue;
+        ck(cudaMemcpyAsync(A.io + k * n3, src[k], sizeof(double) * n3,
+                           cudaMemcpyHostToDevice, ctx->s),
+           "copy cotangent");
+        *dst[k] = A.io + k * n3;
+      }
     }
-    launch_adj_seed(A.n, dgr, dgv, A.C, ctx->s);
+    launch_adj_seed(A.n, dgr, dgv, dga, A.C, ctx->s);
     A.launches += 1;
     rc = backward_impl(ctx, A);
     if (rc) return rc;
-    return vjp_out(ctx, A, g_r0, g_v0, g_m, device_ptrs != 0);
+    return vjp_out(ctx, A, g_r0, g_v0, g_a0, g_m, device_ptrs != 0);
   } catch (const CudaFail& f) {
     return cuda_fail(ctx, f);
   }
+}
+
+int tsbts_adjoint_vjp(tsbts_ctx* ctx, const double* gr_T, const double* gv_T,
+                      double* g_r0, double* g_v0, double* g_m,
+                      int device_ptrs) {
+  return tsbts_adjoint_vjp_state(ctx, gr_T, gv_T, nullptr, g_r0, g_v0,
+                                 nullptr, g_m, device_ptrs);
 }
 
 int tsbts_adjoint_loss_grad(tsbts_ctx* ctx, const double* m, const double* r0,
@@ -925,7 +1011,7 @@ int tsbts_adjoint_loss_grad(tsbts_ctx* ctx, const double* m, const double* r0,
          "copy loss");
     rc = backward_impl(ctx, A);
     if (rc) return rc;
-    return vjp_out(ctx, A, g_r0, g_v0, g_m, device_ptrs != 0);
+    return vjp_out(ctx, A, g_r0, g_v0, nullptr, g_m, device_ptrs != 0);
   } catch (const CudaFail& f) {
     return cuda_fail(ctx, f);
   }

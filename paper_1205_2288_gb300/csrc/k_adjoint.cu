@@ -166,7 +166,7 @@ __device__ __forceinline__ int q_place(const AdjRecs& R, const AdjPass& Q,
                                        long long& ra, long long& rb) {
   ra = cur;
   rb = -1;
-  const long long ta = cur < 0 ? 0 : R.tau[cur];
+  const long long ta = cur < 0 ? R.tau0[j] : R.tau[cur];
   if (cur >= 0 && ta == T) {
     for (int c = 0; c < 3; ++c) p[c] = R.r[c][cur];
     return 1;
@@ -187,9 +187,13 @@ __device__ __forceinline__ int q_place(const AdjRecs& R, const AdjPass& Q,
 // Forward replay
 // ---------------------------------------------------------------------
 
+// a_in / tau_in: the era-start accelerations and ticks of a general start
+// state (nullptr: zero, the initial force following)
 __global__ void adj_load_kernel(int n, const double* m_in, const double* r_in,
-                                const double* v_in, int mixed, double* m_out,
-                                AdjState St, AdjPred P, int* err) {
+                                const double* v_in, const double* a_in,
+                                const long long* tau_in, int mixed,
+                                double* m_out, AdjState St, AdjPred P,
+                                int* err) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
     const double m = m_in[j];
@@ -198,14 +202,15 @@ __global__ void adj_load_kernel(int n, const double* m_in, const double* r_in,
     double p[3];
     for (int c = 0; c < 3; ++c) {
       const double r = r_in[3LL * j + c], v = v_in[3LL * j + c];
-      ok = ok && isfinite(r) && isfinite(v);
+      const double a = a_in ? a_in[3LL * j + c] : 0.0;
+      ok = ok && isfinite(r) && isfinite(v) && isfinite(a);
       St.r[c][j] = r;
       St.v[c][j] = v;
-      St.a[c][j] = 0.0;
+      St.a[c][j] = a;
       P.p[c][j] = r;
       p[c] = r;
     }
-    St.tau[j] = 0;
+    St.tau[j] = tau_in ? tau_in[j] : 0;
     if (mixed) {
       float4 hi, lo;
       pack_ds(p[0], p[1], p[2], (float)m, hi, lo);
@@ -479,7 +484,7 @@ __global__ void adj_back_step_kernel(int n, double inv_ticks, int mixed,
           for (int c = 0; c < 3; ++c) *ar[c] += gp[c];
         } else {
           const long long rb = Rc.rb[j];
-          const long long ta = ra < 0 ? 0 : Rc.tau[ra];
+          const long long ta = ra < 0 ? Rc.tau0[j] : Rc.tau[ra];
           const HermiteW w = hermite_weights(ta, Rc.tau[rb], F.T, inv_ticks);
           for (int c = 0; c < 3; ++c) {
             double* av = ra < 0 ? Q.g0v[c] + j : Rc.gv[c] + ra;
@@ -1186,13 +1191,13 @@ __global__ void adj_loss_seed_kernel(int n, const double* m, AdjState St,
 }
 
 __global__ void adj_seed_kernel(int n, const double* gr, const double* gv,
-                                AdjCot C) {
+                                const double* ga, AdjCot C) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += gridDim.x * blockDim.x) {
     for (int c = 0; c < 3; ++c) {
       C.gr[c][j] = gr ? gr[3LL * j + c] : 0.0;
       C.gv[c][j] = gv ? gv[3LL * j + c] : 0.0;
-      C.ga[c][j] = 0.0;
+      C.ga[c][j] = ga ? ga[3LL * j + c] : 0.0;
     }
     C.gm[j] = 0.0;
   }
@@ -1254,11 +1259,13 @@ VjpShape vjp_shape(int n, int n_act, int sms) {
 }
 
 void launch_adj_load(int n, const double* m_in, const double* r_in,
-                     const double* v_in, int mixed, double* m_out,
+                     const double* v_in, const double* a_in,
+                     const long long* tau_in, int mixed, double* m_out,
                      const AdjState& St, const AdjPred& P, int* err,
                      cudaStream_t s) {
-  adj_load_kernel<<<grid_for(n), 256, 0, s>>>(n, m_in, r_in, v_in, mixed,
-                                              m_out, St, P, err);
+  adj_load_kernel<<<grid_for(n), 256, 0, s>>>(n, m_in, r_in, v_in, a_in,
+                                              tau_in, mixed, m_out, St, P,
+                                              err);
 }
 
 void launch_adj_init_accel(int n, const double* part, const int* nsplit,
@@ -1359,8 +1366,8 @@ void launch_adj_loss(int n, const double* m, const AdjState& St, double* out,
 }
 
 void launch_adj_seed(int n, const double* gr, const double* gv,
-                     const AdjCot& C, cudaStream_t s) {
-  adj_seed_kernel<<<grid_for(n), 256, 0, s>>>(n, gr, gv, C);
+                     const double* ga, const AdjCot& C, cudaStream_t s) {
+  adj_seed_kernel<<<grid_for(n), 256, 0, s>>>(n, gr, gv, ga, C);
 }
 
 void launch_soa_to_aos(int n, double* const src[3], double* dst,

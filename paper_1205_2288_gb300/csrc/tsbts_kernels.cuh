@@ -150,7 +150,8 @@ struct AdjBackPrep {
 // Records of an era's passes (adjoint through every pass, Sec. 2): the
 // position and velocity of each schedule entry's body after its step,
 // their cotangents, the block tick of every entry and the entry links. A
-// body's era-start state (r0, v0) is its record at tick 0 in every pass.
+// body's era-start state (r0, v0 at tick tau0) is its first record in
+// every pass.
 // kind/ra/rb: how each body that is not active was placed at the step
 // being reversed (0: Eq. 2 from its own state; 1: record ra; 2: cubic
 // Hermite between records ra and rb; ra = -1 is the era-start record).
@@ -160,6 +161,7 @@ struct AdjRecs {
   double* gr[3];
   double* gv[3];
   const long long* tau;
+  const long long* tau0;  // era-start tick of each body
   const long long* next_e;
   const long long* prev_e;
   const double* r0[3];
@@ -185,8 +187,11 @@ struct AdjPass {
   double* g0v[3];
 };
 
+// the era-start state: (m, r, v) at tick 0 (a_in, tau_in nullptr; the
+// initial force follows) or a general state with accelerations and ticks
 void launch_adj_load(int n, const double* m_in, const double* r_in,
-                     const double* v_in, int mixed, double* m_out,
+                     const double* v_in, const double* a_in,
+                     const long long* tau_in, int mixed, double* m_out,
                      const AdjState& St, const AdjPred& P, int* err,
                      cudaStream_t s);
 // initial accelerations from the force partials, then the prediction to
@@ -241,9 +246,9 @@ void launch_adj_vjp(int mixed, int n, int n_act, const int* idx, double eps2,
 // seeds dL/dr, dL/dm (velocity and acceleration cotangents zero)
 void launch_adj_loss(int n, const double* m, const AdjState& St, double* out,
                      const AdjCot& C, cudaStream_t s);
-// seeds from (n, 3) cotangents of the final r and v (nullable: zero)
+// seeds from (n, 3) cotangents of the final r, v and a (nullable: zero)
 void launch_adj_seed(int n, const double* gr, const double* gv,
-                     const AdjCot& C, cudaStream_t s);
+                     const double* ga, const AdjCot& C, cudaStream_t s);
 // three structure-of-arrays components -> row-major (n, 3)
 void launch_soa_to_aos(int n, double* const src[3], double* dst,
                        cudaStream_t s);

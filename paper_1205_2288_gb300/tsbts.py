@@ -44,7 +44,8 @@ EXPORTS = (
     "tsbts_init_ensemble", "tsbts_ensemble_energy", "tsbts_adjoint_init",
     "tsbts_adjoint_forward", "tsbts_adjoint_vjp", "tsbts_adjoint_loss_grad",
     "tsbts_adjoint_get_stats", "tsbts_step_estimates", "tsbts_set_state",
-    "tsbts_pipe_peak", "tsbts_adjoint_init_era",
+    "tsbts_pipe_peak", "tsbts_adjoint_init_era", "tsbts_adjoint_forward_state",
+    "tsbts_adjoint_vjp_state",
 )
 
 
@@ -140,6 +141,10 @@ def lib():
                                              I64P, I64P, I32P, I64]
         L.tsbts_adjoint_forward.argtypes = [VP, VP, VP, VP, VP, VP, C.c_int]
         L.tsbts_adjoint_vjp.argtypes = [VP, VP, VP, VP, VP, VP, C.c_int]
+        L.tsbts_adjoint_forward_state.argtypes = [VP, VP, VP, VP, VP, VP, VP,
+                                                  VP, VP, VP, C.c_int]
+        L.tsbts_adjoint_vjp_state.argtypes = [VP, VP, VP, VP, VP, VP, VP, VP,
+                                              C.c_int]
         L.tsbts_adjoint_loss_grad.argtypes = [VP, VP, VP, VP, VP, VP, VP, VP,
                                               C.c_int]
         L.tsbts_adjoint_get_stats.argtypes = [VP,
@@ -496,6 +501,45 @@ def tsbts_adjoint_vjp(ctx, gr_T, gv_T, g_r0=None, g_v0=None, g_m=None,
     return g_r0, g_v0, g_m
 
 
+def tsbts_adjoint_forward_state(ctx, m, r0, v0, a0=None, tau0=None,
+                                device=False):
+    """Forward replay from a general era-start state (host numpy): body j
+    at tick tau0[j] with acceleration a0[j]; a0 None: tick 0 and the force
+    at r0. Returns the final (r, v, a, tau)."""
+    m, r0, v0 = (np.ascontiguousarray(x, np.float64) for x in (m, r0, v0))
+    n = m.shape[0]
+    if device:
+        raise ValueError("tsbts_adjoint_forward_state takes host arrays")
+    a0 = None if a0 is None else np.ascontiguousarray(a0, np.float64)
+    tau0 = None if tau0 is None else np.ascontiguousarray(tau0, np.int64)
+    for x, shape in ((r0, (n, 3)), (v0, (n, 3)), (a0, (n, 3)), (tau0, (n,))):
+        if x is not None and x.shape != shape:
+            raise ValueError("start state arrays must be (n, 3) or (n,)")
+    r_T, v_T, a_T = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
+    tau_T = np.zeros(n, np.int64)
+    _check(lib().tsbts_adjoint_forward_state(
+        ctx, m.ctypes.data, r0.ctypes.data, v0.ctypes.data,
+        None if a0 is None else a0.ctypes.data,
+        None if tau0 is None else tau0.ctypes.data, r_T.ctypes.data,
+        v_T.ctypes.data, a_T.ctypes.data, tau_T.ctypes.data, 0), ctx)
+    return r_T, v_T, a_T, tau_T
+
+
+def tsbts_adjoint_vjp_state(ctx, n, gr_T=None, gv_T=None, ga_T=None):
+    """Reverse mode with cotangents of the final r, v, a (host numpy, None:
+    zero): (g_r0, g_v0, g_a0, g_m)."""
+    gs = [None if g is None else np.ascontiguousarray(g, np.float64)
+          for g in (gr_T, gv_T, ga_T)]
+    for g in gs:
+        if g is not None and g.shape != (n, 3):
+            raise ValueError("cotangents must be (n, 3)")
+    out = [np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)]
+    _check(lib().tsbts_adjoint_vjp_state(
+        ctx, *[None if g is None else g.ctypes.data for g in gs],
+        *[x.ctypes.data for x in out], 0), ctx)
+    return tuple(out)
+
+
 def tsbts_adjoint_loss_grad(ctx, m, r0, v0, loss=None, g_r0=None, g_v0=None,
                             g_m=None, device=False):
     """L = sum m |r(T)|^2 / sum m and its gradient (L, g_r0, g_v0, g_m)."""
@@ -646,6 +690,69 @@ class Ensemble(Simulation):
         return tsbts_ensemble_energy(self.ctx, self.n_clusters)
 
 
+class ErasAdjoint:
+    """Adjoint across consecutive eras of one run: one Adjoint through
+    every pass of each era, era k replayed from the state (r, v, a, tick)
+    that era k - 1 left; reverse mode chains the eras last to first.
+
+    eras = [passes of era 0, passes of era 1, ...], each as for
+    Adjoint(passes=...) (e.g. era_pass_schedules(log, k)). Keyword
+    arguments go to every Adjoint."""
+
+    def __init__(self, n, eps, eras, **kw):
+        self.n = int(n)
+        self.adj = []
+        try:
+            for passes in eras:
+                self.adj.append(Adjoint(n, eps, passes=passes, **kw))
+        except Exception:
+            self.close()
+            raise
+
+    def forward(self, m, r0, v0):
+        """Final (r, v, a, tau) after the last era."""
+        state = (r0, v0, None, None)
+        for a in self.adj:
+            state = a.forward_state(m, *state)
+        return state
+
+    def vjp(self, gr_T=None, gv_T=None, ga_T=None):
+        """(g_r0, g_v0, g_m) of the initial state for cotangents of the
+        last era's final r, v, a; needs forward() first."""
+        g = (gr_T, gv_T, ga_T)
+        g_m = np.zeros(self.n)
+        for a in reversed(self.adj):
+            gr, gv, ga, gm = a.vjp_state(*g)
+            g_m += gm
+            g = (gr, gv, ga)
+        return g[0], g[1], g_m
+
+    def loss_grad(self, m, r0, v0):
+        """L = sum m |r(T)|^2 / sum m after the last era, with its gradient
+        (L, g_r0, g_v0, g_m)."""
+        m = np.ascontiguousarray(m, np.float64)
+        rT = self.forward(m, r0, v0)[0]
+        M = m.sum()
+        r2 = (rT * rT).sum(1)
+        L = float((m * r2).sum() / M)
+        g_r0, g_v0, g_m = self.vjp(2.0 * m[:, None] * rT / M)
+        return L, g_r0, g_v0, g_m + (r2 - L) / M
+
+    def stats(self):
+        return [a.stats() for a in self.adj]
+
+    def close(self):
+        for a in self.adj:
+            a.close()
+        self.adj = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class Adjoint:
     """Adjoint of a frozen block schedule (tsbts_adjoint_*): replay of the
     schedule from (m, r0, v0) and reverse-mode gradients.
@@ -692,6 +799,12 @@ class Adjoint:
 
     def loss_grad(self, m, r0, v0):
         return tsbts_adjoint_loss_grad(self.ctx, m, r0, v0)
+
+    def forward_state(self, m, r0, v0, a0=None, tau0=None):
+        return tsbts_adjoint_forward_state(self.ctx, m, r0, v0, a0, tau0)
+
+    def vjp_state(self, gr_T=None, gv_T=None, ga_T=None):
+        return tsbts_adjoint_vjp_state(self.ctx, self.n, gr_T, gv_T, ga_T)
 
     def stats(self):
         return tsbts_adjoint_get_stats(self.ctx)

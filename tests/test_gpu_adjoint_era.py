@@ -335,3 +335,184 @@ def test_torch_autograd_through_every_pass():
                                         rtol=1e-5)
     finally:
         adj.close()
+
+
+# ---------------------------------------------------------------------
+# Across eras: each era replayed from the state (r, v, a, tick) the era
+# before it left, bodies whose step overshot the era end waiting behind it
+# (Sec. 3); reverse mode chained era by era.
+# ---------------------------------------------------------------------
+
+def waiting_system(n, seed):
+    """A Plummer sphere plus one far, slow body whose step (dt_max = 1/8)
+    overshoots the eras of 1/16: later eras start with bodies at different
+    ticks."""
+    m = inputs.salpeter_masses(n, seed)
+    _, r, v = inputs.plummer(n, seed + 1, masses=m)
+    m = np.append(m, 2e-3)
+    r = np.vstack([r, [30.0, -8.0, 4.0]])
+    v = np.vstack([v, [0.0, 0.03, 0.01]])
+    return m, r, v
+
+
+@pytest.fixture(scope="module")
+def eras_case():
+    m, r, v = waiting_system(300, 41)
+    s = oracle.Sim(m, r, v, eps=0.02, eta=0.05, dt_max=1 / 8, n_iter=3,
+                   era_mode=0, era_log2=4, k_max=K_MAX, log=True)
+    s.run(0.25)
+    st = s.state()
+    sched = s.schedule()
+    s.close()
+    eras = [oracle.era_passes(sched, k)
+            for k in range(len(np.unique(sched["era"])))]
+    (rT, vT, aT, tauT), starts = oracle.eras_replay(m, r, v, 0.02, K_MAX,
+                                                    eras)
+    L, g_rT, g_mL = oracle.loss_msr(m, rT)
+    gr, gv, gm = oracle.eras_replay_vjp(m, r, v, 0.02, K_MAX, eras, g_rT,
+                                        np.zeros_like(g_rT))
+    return dict(m=m, r=r, v=v, eras=eras, starts=starts, st=st, rT=rT,
+                vT=vT, aT=aT, tauT=tauT, L=L, gr=gr, gv=gv, gm=gm + g_mL)
+
+
+def test_eras_case_has_waiting_bodies(eras_case):
+    c = eras_case
+    assert len(c["eras"]) == 4
+    n = len(c["m"])
+    # eras 1 and 3 start with the far body (and a few outer ones) still at
+    # the tick before the era start; era 2 starts synchronised
+    for k, waits in ((1, True), (2, False), (3, True)):
+        tau0 = c["starts"][k][3]
+        era_start = min(p[0][0] for p in c["eras"][k]) >> 16 << 16
+        assert (tau0[n - 1] < era_start) == waits
+        assert ((tau0 < era_start).sum() > 1) == waits
+
+
+def test_fp64_state_replay_and_vjp_per_era(eras_case):
+    c = eras_case
+    rng = np.random.default_rng(21)
+    n = len(c["m"])
+    for k in (1, 3):
+        r0, v0, a0, tau0 = c["starts"][k]
+        passes = c["eras"][k]
+        want = oracle.era_replay_state(c["m"], r0, v0, a0, tau0, 0.02, K_MAX,
+                                       passes)
+        g = [rng.standard_normal((n, 3)) for _ in range(3)]
+        want_g = oracle.era_replay_state_vjp(c["m"], r0, v0, a0, tau0, 0.02,
+                                             K_MAX, passes, *g)
+        for K in (0, 6):
+            with tsbts.Adjoint(n, 0.02, passes=passes,
+                               checkpoint_every=K) as adj:
+                got = adj.forward_state(c["m"], r0, v0, a0, tau0)
+                got_g = adj.vjp_state(*g)
+            for a, b in zip(got, want):
+                np.testing.assert_array_equal(a, b)
+            for a, b in zip(got_g, want_g):
+                assert rel(a, b) < 1e-10, (k, K, rel(a, b))
+
+
+def test_lone_pass_state_replay(eras_case):
+    """One pass from a general start state (the plain block-step adjoint of
+    a later era's final pass)."""
+    c = eras_case
+    n = len(c["m"])
+    r0, v0, a0, tau0 = c["starts"][2]
+    one = [c["eras"][2][-1]]
+    want = oracle.era_replay_state(c["m"], r0, v0, a0, tau0, 0.02, K_MAX, one)
+    gr = np.random.default_rng(22).standard_normal((n, 3))
+    want_g = oracle.era_replay_state_vjp(c["m"], r0, v0, a0, tau0, 0.02,
+                                         K_MAX, one, gr, None, gr)
+    with tsbts.Adjoint(n, 0.02, one[0]) as adj:
+        got = adj.forward_state(c["m"], r0, v0, a0, tau0)
+        got_g = adj.vjp_state(gr, None, gr)
+    for a, b in zip(got, want):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(got_g, want_g):
+        assert rel(a, b) < 1e-10, rel(a, b)
+
+
+def test_fp64_eras_adjoint_matches_oracle(eras_case):
+    c = eras_case
+    n = len(c["m"])
+    with tsbts.ErasAdjoint(n, 0.02, c["eras"]) as ea:
+        rT, vT, aT, tauT = ea.forward(c["m"], c["r"], c["v"])
+        L, gr, gv, gm = ea.loss_grad(c["m"], c["r"], c["v"])
+    for a, b in ((rT, c["rT"]), (vT, c["vT"]), (aT, c["aT"]),
+                 (tauT, c["tauT"]), (rT, c["st"]["r"]), (tauT, c["st"]["tau"])):
+        np.testing.assert_array_equal(a, b)
+    assert abs(L / c["L"] - 1) < 1e-14
+    for a, b in ((gr, c["gr"]), (gv, c["gv"]), (gm, c["gm"])):
+        assert rel(a, b) < 1e-10, rel(a, b)
+
+
+def test_mixed_eras_adjoint_within_fp32_accuracy(eras_case):
+    c = eras_case
+    n = len(c["m"])
+    with tsbts.ErasAdjoint(n, 0.02, c["eras"],
+                           precision=tsbts.TSBTS_MIXED) as ea:
+        L, gr, gv, gm = ea.loss_grad(c["m"], c["r"], c["v"])
+    assert abs(L / c["L"] - 1) < 1e-7
+    for a, b in ((gr, c["gr"]), (gv, c["gv"]), (gm, c["gm"])):
+        assert rel(a, b) < 1e-4, rel(a, b)
+
+
+def test_state_start_errors(eras_case):
+    c = eras_case
+    n = len(c["m"])
+    r0, v0, a0, tau0 = c["starts"][1]
+    passes = c["eras"][1]
+    first = min(p[0][0] for p in passes)
+    with tsbts.Adjoint(n, 0.02, passes=passes) as adj:
+        late = tau0.copy()
+        late[0] = first
+        for bad, what in (((a0, late), "tick at a block tick"),
+                          ((a0, tau0 - tau0.max() - 1), "negative tick")):
+            with pytest.raises(tsbts.TsbtsError) as e:
+                adj.forward_state(c["m"], r0, v0, *bad)
+            assert e.value.code == tsbts.TSBTS_ERR_ARG, what
+        ctx = adj.ctx
+        with pytest.raises(tsbts.TsbtsError) as e:
+            tsbts._check(tsbts.lib().tsbts_adjoint_forward_state(
+                ctx, c["m"].ctypes.data, r0.ctypes.data, v0.ctypes.data,
+                None, tau0.ctypes.data, None, None, None, None, 0), ctx)
+        assert e.value.code == tsbts.TSBTS_ERR_ARG
+        # still usable
+        got = adj.forward_state(c["m"], r0, v0, a0, tau0)
+    want = oracle.era_replay_state(c["m"], r0, v0, a0, tau0, 0.02, K_MAX,
+                                   passes)
+    np.testing.assert_array_equal(got[0], want[0])
+
+
+def test_gpu_schedule_eras_gradient_matches_central_differences():
+    """Four eras of a Plummer n = 2048 run (plus a far, waiting body) from
+    the FP64 GPU integrator's own schedule log: the gradient across the
+    eras against central differences of the FP64 replay."""
+    m, r, v = waiting_system(2048, 51)
+    n = len(m)
+    sim = tsbts.Simulation(m, r, v, eps=0.01, eta=0.02, dt_max=1 / 8,
+                           n_iter=3, era_mode=0, era_log2=4)
+    sim.schedule_log(20_000_000)
+    sim.step_era(0.25)
+    st = sim.state()
+    eras = [tsbts.era_pass_schedules(sim.schedule(), k) for k in range(4)]
+    sim.close()
+    rng = np.random.default_rng(23)
+    with tsbts.ErasAdjoint(n, 0.01, eras) as ea:
+        rT = ea.forward(m, r, v)[0]
+        np.testing.assert_array_equal(rT, st["r"])
+        L, gr, gv, gm = ea.loss_grad(m, r, v)
+
+        def loss(m_, r_, v_):
+            x = ea.forward(m_, r_, v_)[0]
+            return float((m_ * (x * x).sum(1)).sum() / m_.sum())
+        h = 1e-6
+        for which, g in (("r", gr), ("v", gv), ("m", gm)):
+            d = rng.standard_normal(g.shape)
+            args = dict(m_=m, r_=r, v_=v)
+            p, q = dict(args), dict(args)
+            p[which + "_"] = args[which + "_"] + h * d
+            q[which + "_"] = args[which + "_"] - h * d
+            fd = (loss(**p) - loss(**q)) / (2 * h)
+            an = float((g * d).sum())
+            assert abs(fd - an) <= 1e-6 * np.linalg.norm(g) * \
+                np.linalg.norm(d), (which, fd, an)
