@@ -24,7 +24,8 @@ JSON line keys beyond the driver contract:
 Run: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
      [--quick] (skip fp64, configs and cpu_baseline)
 Other modes: --force-sweep (force kernel alone), --ensemble (512 clusters),
---adjoint (gradient through a frozen block schedule, Plummer n = 8192).
+--adjoint (gradient through a frozen block schedule, Plummer n = 8192),
+--study (the paper's Sec. 3-4 era / iteration study, long spans).
 """
 from __future__ import annotations
 
@@ -541,6 +542,153 @@ def ensemble_bench(args):
     return 0
 
 
+def study_job(job, span):
+    """One run of the long-integration study: an ensemble of models with a
+    fixed era (one cluster per model) or one model with a dynamic era,
+    stepped time unit by time unit to `span`; returns each model's largest
+    relative energy error over the run and its error at the end."""
+    import numpy as np
+
+    from paper_1205_2288_gb300 import inputs, tsbts
+
+    prec = tsbts.TSBTS_MIXED if job["precision"] == "mixed" else \
+        tsbts.TSBTS_FP64
+    models = [inputs.plummer(job["n"], s) for s in job["seeds"]]
+    t0 = time.perf_counter()
+    if job["era"] == "dynamic":
+        (m, r, v), = models
+        g = tsbts.Simulation(m, r, v, eps=job["eps"], eta=job["eta"],
+                             dt_max=job["dt_max"], n_iter=job["n_iter"],
+                             era_mode=1, precision=prec)
+
+        def energies():
+            return np.array([sum(g.energy())])
+    else:
+        off = np.cumsum([0] + [len(x[0]) for x in models])
+        g = tsbts.Ensemble(off, np.concatenate([x[0] for x in models]),
+                           np.vstack([x[1] for x in models]),
+                           np.vstack([x[2] for x in models]),
+                           eps=np.full(len(models), job["eps"]),
+                           eta=job["eta"], dt_max=job["dt_max"],
+                           n_iter=job["n_iter"], era_log2=job["era_log2"],
+                           precision=prec)
+
+        def energies():
+            ek, ep = tsbts.tsbts_ensemble_energy(g.ctx, len(models))
+            return ek + ep
+    try:
+        e0 = energies()
+        worst = np.zeros(len(models))
+        for t in range(1, span + 1):
+            g.step_era(float(t))
+            err = np.abs(energies() - e0) / np.abs(e0)
+            worst = np.maximum(worst, err)
+        steps = g.stats()["block_steps"]
+    finally:
+        g.close()
+    return dict(job, worst=worst.tolist(), at_end=err.tolist(),
+                block_steps=int(steps), seconds=time.perf_counter() - t0)
+
+
+def study(args):
+    """The paper's long-integration era and iteration study on the GPU
+    (Sec. 3: energy error against era size and pass count, 100-body models
+    with eta = 0.1 and 500-body models with eta = 0.5, eps = 0.01, dt_max =
+    1/64; Sec. 4: dynamic against fixed era of 1/64, three passes), in FP64
+    and in mixed precision. Seeded Plummer models stand in for the paper's
+    unpublished ones (the 100-body seeds are the oracle reruns' own, so the
+    FP64 runs repeat those bit for bit). Every configuration's runs go on
+    their own context and stream, many at a time."""
+    import concurrent.futures as cf
+    import math
+
+    with open(os.path.join(ROOT, "tests", "golden",
+                           "sec3_energy_experiment.json")) as f:
+        sec3 = json.load(f)
+    with open(os.path.join(ROOT, "tests", "golden",
+                           "sec4_dynamic_era.json")) as f:
+        sec4 = json.load(f)
+    span = args.study_span
+    precs = ["fp64", "mixed"] if args.study_precision == "both" else \
+        [args.study_precision]
+    base = dict(eps=sec3["eps_plummer"], dt_max=sec3["dt_max"])
+    jobs = []
+    for prec in precs:
+        # Sec. 3, 100 bodies: five era sizes, three and five passes
+        for n_iter in (3, 5):
+            for era in sec3["era_sizes_in_figures"]:
+                jobs.append(dict(base, study="sec3_n100", precision=prec,
+                                 n=sec3["n_bodies"], eta=sec3["eta"],
+                                 n_iter=n_iter, era=era,
+                                 era_log2=round(-math.log2(era)),
+                                 seeds=[1000 + k for k in range(
+                                     sec3["n_realisations"])]))
+        # Sec. 3, 500 bodies, eta = 0.5: seven era sizes, three passes
+        for k in range(7):
+            jobs.append(dict(base, study="sec3_n500", precision=prec, n=500,
+                             eta=0.5, n_iter=3, era=2.0 ** -k, era_log2=k,
+                             seeds=[3000 + j for j in range(5)]))
+        # Sec. 4: ten models, fixed era 1/64 against the dynamic era
+        for n, eta, s0 in ((sec4["n_bodies"], sec4["eta"], 2000),
+                           (500, 0.5, 4000)):
+            seeds = [s0 + k for k in range(sec4["n_realisations"])]
+            tag = f"sec4_n{n}"
+            jobs.append(dict(base, study=tag, precision=prec, n=n, eta=eta,
+                             n_iter=sec4["n_iter"], era=sec4["fixed_era"],
+                             era_log2=round(-math.log2(sec4["fixed_era"])),
+                             seeds=seeds))
+            for sd in seeds:
+                jobs.append(dict(base, study=tag, precision=prec, n=n,
+                                 eta=eta, n_iter=sec4["n_iter"],
+                                 era="dynamic", seeds=[sd]))
+    # the 500-body and dynamic runs take longest: start them first
+    jobs.sort(key=lambda j: (-j["n"], j["era"] != "dynamic"))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=args.study_workers) as ex:
+        done = list(ex.map(lambda j: study_job(j, span), jobs))
+    wall = time.perf_counter() - t0
+
+    def geo(x):
+        return math.exp(sum(math.log(v) for v in x) / len(x))
+    out = {}
+    for prec in precs:
+        res = {}
+        for d in done:
+            if d["precision"] != prec or not d["study"].startswith("sec3"):
+                continue
+            res.setdefault(d["study"], {})[
+                f"passes{d['n_iter']}_era{d['era']}"] = {
+                "worst_max": max(d["worst"]),
+                "worst_median": statistics.median(d["worst"]),
+                "block_steps": d["block_steps"]}
+        for tag in ("sec4_n100", "sec4_n500"):
+            fixed = [d for d in done if d["precision"] == prec and
+                     d["study"] == tag and d["era"] != "dynamic"][0]
+            dyn = sorted((d for d in done if d["precision"] == prec and
+                          d["study"] == tag and d["era"] == "dynamic"),
+                         key=lambda d: d["seeds"][0])
+            ratio = [dd["worst"][0] / fw
+                     for dd, fw in zip(dyn, fixed["worst"])]
+            res[tag] = {"dynamic_at_most_fixed": sum(x <= 1 for x in ratio),
+                        "models": len(ratio),
+                        "geomean_ratio_dynamic_over_fixed": geo(ratio),
+                        "worst_fixed": max(fixed["worst"]),
+                        "worst_dynamic": max(dd["worst"][0] for dd in dyn),
+                        "block_steps_fixed": fixed["block_steps"],
+                        "block_steps_dynamic": sum(dd["block_steps"]
+                                                   for dd in dyn)}
+        out[prec] = res
+    line = {"metric": "long-integration era / iteration study "
+                      "(largest relative energy error over the run)",
+            "span_time_units": span, "runs": len(done),
+            "models": sum(len(d["seeds"]) for d in done),
+            "wall_seconds": wall, "results": out,
+            "note": "seeded Plummer models stand in for the paper's; energy "
+                    "sampled at every time unit"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def adjoint_bench(args):
     """Gradient of the mass-weighted mean-square radius at the end of one
     era with respect to the initial positions, velocities and masses,
@@ -730,6 +878,14 @@ def main():
     ap.add_argument("--ensemble", action="store_true",
                     help="integrate the 512-cluster ensemble instead")
     ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--study", action="store_true",
+                    help="the paper's long era / iteration study (Sec. 3-4)")
+    ap.add_argument("--study-span", type=int, default=100,
+                    help="--study: time units per run (the paper: 1000)")
+    ap.add_argument("--study-precision", default="both",
+                    choices=["both", "fp64", "mixed"])
+    ap.add_argument("--study-workers", type=int, default=32,
+                    help="--study: runs in flight at once")
     ap.add_argument("--adjoint", action="store_true",
                     help="gradient through a frozen block schedule")
     ap.add_argument("--schedule-out", default="",
@@ -750,6 +906,8 @@ def main():
         return ensemble_bench(args)
     if args.adjoint:
         return adjoint_bench(args)
+    if args.study:
+        return study(args)
     ws, rank, local = dist_env()
     dist = init_dist(ws)
     if args.impl == "reference":
