@@ -446,7 +446,7 @@ void setup_bodies(tsbts_ctx* c, int n) {
   B.seg_ta = dalloc<long long>(L, n);
   B.seg_tb = dalloc<long long>(L, n);
   B.seg = dalloc<double>(L, 18 * (size_t)n);
-  B.part_cap = std::max<long long>(c->fl.part_cap, 5LL * n);
+  B.part_cap = force_partial_capacity(c->fl, n);
   B.part = dalloc<double>(L, B.part_cap);
   Bodies& S = c->snap;
   S = Bodies{};
@@ -652,8 +652,12 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
       ck(autotune_mixed_plans(c->cfg.device, base, c->fl, c->d_nsplit, c->s,
                               &t),
          "force plan autotuning");
+      // (a tuned plan is used only where its partial sums fit this
+      // context's buffer)
       const std::vector<int> b = plan_buckets(c->n);
-      for (size_t k = 0; k < b.size(); ++k) c->pt.b[k] = t[b[k]];
+      for (size_t k = 0; k < b.size(); ++k)
+        if ((long long)t[b[k]].S * 5 * b[k] <= c->B.part_cap)
+          c->pt.b[k] = t[b[k]];
     }
     c->inited = true;
     c->graph_dirty = true;
@@ -1138,8 +1142,8 @@ int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
     Scratch& S = g_scratch[dev];
     // partial sums of up to n active bodies: the plan tuner times active
     // counts up to n, whatever this call's n_act
-    const long long need_part =
-        std::max<long long>(fl.part_cap, 5LL * std::max<int64_t>(n_act, n));
+    const long long need_part = std::max<long long>(
+        force_partial_capacity(fl, n), 5LL * std::max<int64_t>(n_act, n));
     if (S.n_cap < n || S.part_cap < need_part) {
       ck(cudaDeviceSynchronize(), "synchronize before scratch growth");
       cudaFree(S.soa);
@@ -1198,6 +1202,8 @@ int tsbts_force(int precision, int exact_order, int64_t n, const double* m,
         std::vector<Plan> t;
         ForceArgs base = fa;
         base.idx = S.iota;
+        // tuned for the capacity every caller with this n has
+        base.part_cap = force_partial_capacity(fl, ni);
         ck(autotune_mixed_plans(dev, base, fl, S.nsplit, s, &t),
            "force plan autotuning");
         tp = tuned_plans(dev, ni, fl.grid);

@@ -291,6 +291,12 @@ ForceLaunch force_launch_shape(int precision, int device) {
   return fl;
 }
 
+long long force_partial_capacity(const ForceLaunch& fl, long long n) {
+  const long long want = std::min<long long>(5LL * 2 * kSplitCap * n,
+                                             1LL << 27);
+  return std::max<long long>(fl.part_cap, want);
+}
+
 cudaError_t launch_force(int precision, const ForceArgs& fa,
                          const ForceLaunch& fl, cudaStream_t s,
                          const PlanTable* pt, bool pdl) {

@@ -371,6 +371,11 @@ struct ForceLaunch {
 };
 
 ForceLaunch force_launch_shape(int precision, int device);
+// Doubles of split partial sums a force launch over n bodies may write: room
+// for every body of n with up to twice the tiled split cap (at most 2^27,
+// at least the grid's own floor). Every caller of one body count uses the
+// same capacity, so plans tuned by one fit the buffers of another.
+long long force_partial_capacity(const ForceLaunch& fl, long long n);
 Plan plan_force(int precision, int exact, int n_act, int n, int grid,
                 long long part_cap);
 // measured plans of the mixed force kernel per active count 0..n (cached
