@@ -133,10 +133,13 @@ int tsbts_init_device(tsbts_ctx* ctx, int64_t n, const double* m_dev,
  * c owns bodies offsets[c] .. offsets[c+1]-1 of the HOST arrays m[n],
  * r[n*3], v[n*3] (n = offsets[n_clusters], offsets[0] = 0, every cluster
  * non-empty, 1 <= n_clusters <= 4096); eps[n_clusters] its softening
- * lengths. eta and dt_max as in tsbts_init. The context must use a fixed
- * era (era_mode 0). Afterwards tsbts_step_era advances every cluster over
- * the same eras; tsbts_state returns all bodies; tsbts_energy returns the
- * sums over the clusters; the schedule log is not recorded. */
+ * lengths. eta and dt_max as in tsbts_init. With a fixed era (era_mode
+ * 0) tsbts_step_era advances every cluster over the same eras; with the
+ * dynamic era (era_mode 1) every cluster takes its own eras (Alg. 3 on its
+ * own bodies, as a lone run of that cluster would), and tsbts_step_era
+ * returns once every cluster has reached t_end. tsbts_state returns all
+ * bodies; tsbts_energy returns the sums over the clusters; the schedule log
+ * is not recorded; converged iteration (conv_tol > 0) is refused. */
 int tsbts_init_ensemble(tsbts_ctx* ctx, int64_t n_clusters,
                         const int64_t* offsets, const double* m,
                         const double* r, const double* v, const double* eps,

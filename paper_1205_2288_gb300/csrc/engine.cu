@@ -313,9 +313,33 @@ long long era_ticks(tsbts_ctx* c) {
                                  c->dtmax_t, c->cfg.dyn_min_log2);
 }
 
+// Dynamic eras of an ensemble: every cluster's next era end (Alg. 3 on its
+// own bodies, capped at tau_end); false once every cluster has reached
+// tau_end.
+bool ensemble_eras(tsbts_ctx* c, long long tau_end) {
+  ck(cudaMemsetAsync(c->E.undone, 0, sizeof(int), c->s), "memset");
+  launch_ens_era(c->B, c->E, c->dtmax_t, c->cfg.dyn_min_log2, tau_end, c->s);
+  c->launches += 1;
+  int undone = 0;
+  ck(cudaMemcpyAsync(&undone, c->E.undone, sizeof undone,
+                     cudaMemcpyDeviceToHost, c->s),
+     "read era state");
+  ck(cudaStreamSynchronize(c->s), "synchronize");
+  return undone > 0;
+}
+
 int step_era_impl(tsbts_ctx* c, long long tau_end) {
+  // an ensemble with dynamic eras runs global eras in which every cluster
+  // takes its own era (a cluster already at tau_end takes none); the
+  // passes' block steps stop at each cluster's own era end
+  const bool own_eras = c->ensemble && c->E.ts;
   while (c->t_sys < tau_end) {
-    const long long tau_e = std::min(c->t_sys + era_ticks(c), tau_end);
+    if (own_eras && !ensemble_eras(c, tau_end)) {
+      c->t_sys = tau_end;
+      break;
+    }
+    const long long tau_e =
+        own_eras ? tau_end : std::min(c->t_sys + era_ticks(c), tau_end);
     launch_copy_state(c->snap, c->B, c->s);
     c->launches += 1;
     // counters at the era start: an era re-run after the history grew
@@ -410,7 +434,12 @@ int step_era_impl(tsbts_ctx* c, long long tau_end) {
       c->launches += 1;
       c->restarts += 1;
     }
-    c->t_sys = tau_e;
+    if (own_eras) {
+      launch_ens_era_end(c->E, c->s);
+      c->launches += 1;
+    } else {
+      c->t_sys = tau_e;
+    }
     c->eras += 1;
   }
   return TSBTS_OK;
@@ -522,6 +551,13 @@ void setup_ensemble(tsbts_ctx* c, const EnsInput& in) {
   c->d_ep = dalloc<double>(L, nc);
   c->efl = ens_force_launch_shape(c->cfg.precision, c->cfg.device);
   E.part_cap = c->B.part_cap;
+  if (c->cfg.era_mode == 1) {
+    // each cluster its own dynamic era, from system time 0
+    E.ts = dalloc<long long>(L, nc);
+    E.te = dalloc<long long>(L, nc);
+    E.undone = dalloc<int>(L, 1);
+    ck(cudaMemsetAsync(E.ts, 0, sizeof(long long) * nc, c->s), "memset");
+  }
   c->nc = nc;
   c->ensemble = true;
 }
@@ -548,8 +584,6 @@ int init_common(tsbts_ctx* c, int64_t n, const double* m, const double* r,
       if (!(ens->eps[k] >= 0.0) || !std::isfinite(ens->eps[k]))
         return fail(c, TSBTS_ERR_ARG, "eps must be finite and >= 0");
     }
-    if (c->cfg.era_mode != 0)
-      return fail(c, TSBTS_ERR_ARG, "ensembles use a fixed era");
     if (c->cfg.conv_tol > 0.0)
       return fail(c, TSBTS_ERR_ARG,
                   "ensembles run the fixed pass count (conv_tol = 0)");

@@ -10,7 +10,9 @@
 // comparison of dynamic and fixed eras (Sec. 4) rules out.
 //
 // Plain C++ with no CUDA dependence, so that the host test suite can
-// compile and check it on its own.
+// compile and check it on its own (the era length is also callable from
+// device code when nvcc compiles it, for ensembles whose clusters each
+// take their own dynamic era).
 #ifndef TSBTS_ERA_RULE_H
 #define TSBTS_ERA_RULE_H
 
@@ -18,9 +20,15 @@
 #include <cstddef>
 #include <cstdint>
 
-inline long long tsbts_dynamic_era_ticks(long long first, long long last,
-                                         long long dt_max_ticks,
-                                         int dyn_min_log2) {
+#ifdef __CUDACC__
+#define TSBTS_HOST_DEVICE __host__ __device__
+#else
+#define TSBTS_HOST_DEVICE
+#endif
+
+inline TSBTS_HOST_DEVICE long long tsbts_dynamic_era_ticks(
+    long long first, long long last, long long dt_max_ticks,
+    int dyn_min_log2) {
   long long lo = dyn_min_log2 < 63 ? dt_max_ticks >> dyn_min_log2 : 0;
   if (lo < 1) lo = 1;
   long long e = last - first;

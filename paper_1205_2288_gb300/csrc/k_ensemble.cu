@@ -16,6 +16,7 @@
 // small clusters do not pay a launch each and big ones keep the grid busy.
 #include <climits>
 
+#include "era_rule.h"
 #include "force_device.cuh"
 #include "step_device.cuh"
 #include "tsbts_kernels.cuh"
@@ -31,7 +32,7 @@ constexpr int kPlanThreads = 1024;
 __global__ void ens_pass_begin_kernel(Ens E, long long tau_s) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < E.nc;
        c += gridDim.x * blockDim.x) {
-    E.tau_c[c] = tau_s;
+    E.tau_c[c] = E.ts ? E.ts[c] : tau_s;
     E.tau_next[c] = 0;
     E.cnt[c] = 0;
     for (int k = 0; k < kMaxLevels; ++k) E.hist[c * kMaxLevels + k] = 0;
@@ -61,6 +62,58 @@ __global__ void ens_pass_setup_kernel(Bodies B, Params P, Ens E,
 }
 
 // ---------------------------------------------------------------------
+// dynamic eras, one per cluster (Alg. 3 with reading R11 on the cluster's
+// own bodies): one block per cluster finds the earliest and latest next
+// block time of its bodies and sets the era end, capped at the end of the
+// integration; a cluster already there gets an empty era
+// ---------------------------------------------------------------------
+constexpr int kEraThreads = 256;
+
+__global__ void __launch_bounds__(kEraThreads)
+    ens_era_kernel(Bodies B, Ens E, long long dtmax_t, int dyn_min_log2,
+                   long long tau_end) {
+  const int c = blockIdx.x;
+  long long lo = LLONG_MAX, hi = LLONG_MIN;
+  for (int i = E.off[c] + threadIdx.x; i < E.off[c + 1]; i += kEraThreads) {
+    const long long t = B.tau[i] + B.dt[i];
+    lo = t < lo ? t : lo;
+    hi = t > hi ? t : hi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long a = __shfl_xor_sync(kFull, lo, o);
+    const long long b = __shfl_xor_sync(kFull, hi, o);
+    lo = a < lo ? a : lo;
+    hi = b > hi ? b : hi;
+  }
+  __shared__ long long s_lo[kEraThreads / 32], s_hi[kEraThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    s_lo[threadIdx.x >> 5] = lo;
+    s_hi[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < kEraThreads / 32; ++w) {
+    lo = s_lo[w] < lo ? s_lo[w] : lo;
+    hi = s_hi[w] > hi ? s_hi[w] : hi;
+  }
+  const long long ts = E.ts[c];
+  if (ts >= tau_end) {
+    E.te[c] = ts;
+    return;
+  }
+  const long long len = tsbts_dynamic_era_ticks(lo, hi, dtmax_t, dyn_min_log2);
+  E.te[c] = ts + len < tau_end ? ts + len : tau_end;
+  atomicAdd(E.undone, 1);
+}
+
+// after the era: every cluster's system time is its era end
+__global__ void ens_era_end_kernel(Ens E) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < E.nc;
+       c += gridDim.x * blockDim.x)
+    E.ts[c] = E.te[c];
+}
+
+// ---------------------------------------------------------------------
 // select: one warp per cluster
 // ---------------------------------------------------------------------
 __global__ void ens_select_kernel(Ens E, Params P) {
@@ -83,7 +136,7 @@ __global__ void ens_select_kernel(Ens E, Params P) {
     }
     const long long D = 1LL << (P.k_max - kk);
     const long long tn = (E.tau_c[c] / D + 1) * D;
-    if (tn > ctl->tau_e) {
+    if (tn > (E.te ? E.te[c] : ctl->tau_e)) {
       E.tau_next[c] = LLONG_MAX;  // finished this pass
     } else {
       E.tau_next[c] = tn;
@@ -559,6 +612,16 @@ ForceLaunch ens_force_launch_shape(int precision, int device) {
   fl.tile_i = kThreads;
   fl.part_cap = 0;
   return fl;
+}
+
+void launch_ens_era(const Bodies& B, const Ens& E, long long dtmax_t,
+                    int dyn_min_log2, long long tau_end, cudaStream_t s) {
+  ens_era_kernel<<<E.nc, kEraThreads, 0, s>>>(B, E, dtmax_t, dyn_min_log2,
+                                              tau_end);
+}
+
+void launch_ens_era_end(const Ens& E, cudaStream_t s) {
+  ens_era_end_kernel<<<blocks_for(E.nc, 128, 1024), 128, 0, s>>>(E);
 }
 
 void launch_ens_pass_begin(const Ens& E, long long tau_s, cudaStream_t s) {

@@ -152,6 +152,13 @@ struct Ens {
                          // still stepping, [3] record base of this step,
                          // [4] items taken by the force launch
   long long part_cap;    // doubles in the partial-sum buffer
+  // dynamic eras (each cluster its own, Alg. 3 on its own bodies): per
+  // cluster the era start and end in ticks, and the count of clusters that
+  // have not reached the end of the integration; nullptr with a fixed era
+  // (one era for all clusters)
+  long long* ts;
+  long long* te;
+  int* undone;
 };
 
 // Work plan of one force launch: IG active bodies per work item (128 / IG

@@ -46,6 +46,12 @@ void launch_energy_predict(const Bodies& B, const Params& P, long long T,
 int ens_max_clusters();
 ForceLaunch ens_force_launch_shape(int precision, int device);
 void launch_ens_pass_begin(const Ens& E, long long tau_s, cudaStream_t s);
+// dynamic eras: each cluster's era end from its bodies' next block times
+// (Alg. 3), capped at tau_end; *E.undone counts the clusters not yet there
+void launch_ens_era(const Bodies& B, const Ens& E, long long dtmax_t,
+                    int dyn_min_log2, long long tau_end, cudaStream_t s);
+// every cluster's era start becomes its era end
+void launch_ens_era_end(const Ens& E, cudaStream_t s);
 void launch_ens_pass_setup(const Bodies& B, const Params& P, const Ens& E,
                            const History& cur, cudaStream_t s);
 // one global block step (five launches); ev0/ev1 (nullable) bracket the

@@ -659,15 +659,18 @@ class Ensemble(Simulation):
     """Independent clusters integrated together (tsbts_init_ensemble).
 
     offsets[c] .. offsets[c+1]-1 are cluster c's bodies; eps[c] its
-    softening. Fixed era only."""
+    softening. era_mode 0: one fixed era of 2^-era_log2 for all clusters;
+    1: every cluster its own dynamic era (Alg. 3 on its own bodies)."""
 
     def __init__(self, offsets, m, r, v, *, eps, eta, dt_max,
-                 precision=TSBTS_FP64, n_iter=3, era_log2=3, k_max=20,
-                 exact_order=-1, device=0, stream=None, graph_steps=32):
+                 precision=TSBTS_FP64, n_iter=3, era_mode=0, era_log2=3,
+                 dyn_min_log2=3, k_max=20, exact_order=-1, device=0,
+                 stream=None, graph_steps=32):
         cfg = tsbts_config_default()
         cfg.precision = precision
         cfg.n_iter = n_iter
-        cfg.era_mode = 0
+        cfg.era_mode = era_mode
+        cfg.dyn_min_log2 = dyn_min_log2
         cfg.era_log2 = era_log2
         cfg.k_max = k_max
         cfg.exact_order = exact_order

@@ -35,11 +35,12 @@ def make_clusters(sizes, seed):
 KW = dict(eta=0.02, dt_max=1 / 8, n_iter=3, era_log2=3, k_max=20)
 
 
-def oracle_clusters(orc, off, m, r, v, eps, t_end, **kw):
+def oracle_clusters(orc, off, m, r, v, eps, t_end, era_mode=0, **kw):
     out = []
     for c in range(len(off) - 1):
         a, b = off[c], off[c + 1]
-        s = orc.Sim(m[a:b], r[a:b], v[a:b], eps=eps[c], era_mode=0, **kw)
+        s = orc.Sim(m[a:b], r[a:b], v[a:b], eps=eps[c], era_mode=era_mode,
+                    **kw)
         e0 = s.energy()
         s.run(t_end)
         out.append((s.state(), e0, s.energy(), s.stats()))
@@ -117,7 +118,8 @@ def test_ensemble_argument_errors():
         assert e.value.code == tsbts.TSBTS_ERR_ARG
     finally:
         tsbts.tsbts_destroy(ctx)
-    cfg.era_mode = 1
+    # every cluster would need its own pass count: refused
+    cfg.conv_tol = 1e-6
     ctx = tsbts.tsbts_create(cfg)
     try:
         with pytest.raises(tsbts.TsbtsError) as e:
@@ -125,6 +127,58 @@ def test_ensemble_argument_errors():
         assert e.value.code == tsbts.TSBTS_ERR_ARG
     finally:
         tsbts.tsbts_destroy(ctx)
+
+
+def scaled_clusters(sizes, scales, seed):
+    """Clusters of different sizes and radii (virial scaling: r by s, v by
+    s^-1/2), so that their block steps and dynamic eras differ."""
+    off, m, r, v, eps = make_clusters(sizes, seed)
+    for c, s in enumerate(scales):
+        a, b = off[c], off[c + 1]
+        r[a:b] *= s
+        v[a:b] /= np.sqrt(s)
+    return off, m, r, v, eps
+
+
+KWD = dict(eta=0.02, dt_max=1 / 8, n_iter=3, dyn_min_log2=3, k_max=20)
+
+
+@pytest.mark.parametrize("graph_steps", [0, 32])
+def test_ensemble_dynamic_eras_fp64_bit_exact_per_cluster(orc, graph_steps):
+    """Dynamic eras (Alg. 3) taken by every cluster on its own bodies: each
+    cluster's state and energies are those of the oracle's lone run of it
+    with the dynamic era, bit for bit, although the clusters take
+    different numbers of eras of different lengths."""
+    sizes = [24, 100, 257, 64, 500, 1]
+    off, m, r, v, eps = scaled_clusters(sizes, [1.0, 0.3, 1.0, 3.0, 1.5,
+                                                1.0], seed=9)
+    ref = []
+    for c in range(len(sizes)):
+        a, b = off[c], off[c + 1]
+        s = orc.Sim(m[a:b], r[a:b], v[a:b], eps=eps[c], era_mode=1, **KWD)
+        e0 = s.energy()
+        s.run(0.25)   # the same two calls as below: era ends at 0.25 too
+        s.run(0.375)
+        ref.append((s.state(), e0, s.energy(), s.stats()))
+    g = tsbts.Ensemble(off, m, r, v, eps=eps, era_mode=1,
+                       graph_steps=graph_steps, **KWD)
+    ek0, ep0 = g.cluster_energy()
+    g.step_era(0.25)
+    g.step_era(0.375)
+    st = g.state()
+    ek, ep = g.cluster_energy()
+    for c in range(len(sizes)):
+        a, b = off[c], off[c + 1]
+        so, e0, e1, _ = ref[c]
+        for key in ("r", "v", "a", "tau", "dt"):
+            np.testing.assert_array_equal(st[key][a:b], so[key],
+                                          err_msg=f"cluster {c} {key}")
+        assert (ek0[c], ep0[c]) == e0
+        assert (ek[c], ep[c]) == e1
+    eras = [x[3]["eras"] for x in ref]
+    assert len(set(eras)) > 1, eras
+    assert g.stats()["interactions"] == sum(x[3]["interactions"] for x in ref)
+    assert st["t"] == 0.375
 
 
 def config4_subset(count=32, seed=7):
@@ -181,4 +235,23 @@ def test_config4_subset_mixed_energy_bar(orc):
         _, e0, e1, _ = ref[c]
         de_o = abs(sum(e1) / sum(e0) - 1.0)
         de_g = abs((ek[c] + ep[c]) / (ek0[c] + ep0[c]) - 1.0)
+        assert de_g <= 2 * de_o + 1e-7, (c, de_g, de_o)
+
+
+def test_ensemble_dynamic_eras_mixed_energy(orc):
+    """Mixed precision with every cluster's own dynamic eras: each cluster's
+    relative energy error within twice its oracle run's (+1e-7)."""
+    sizes = [64, 300, 1000, 128]
+    off, m, r, v, eps = scaled_clusters(sizes, [1.0, 0.5, 1.0, 2.0], seed=11)
+    kw = dict(KWD, eta=0.01)
+    ref = oracle_clusters(orc, off, m, r, v, eps, 0.125, era_mode=1, **kw)
+    g = tsbts.Ensemble(off, m, r, v, eps=eps, era_mode=1,
+                       precision=tsbts.TSBTS_MIXED, **kw)
+    ek0, ep0 = g.cluster_energy()
+    g.step_era(0.125)
+    ek, ep = g.cluster_energy()
+    for c in range(len(sizes)):
+        _, e0, e1, _ = ref[c]
+        de_o = abs(sum(e1) / sum(e0) - 1)
+        de_g = abs((ek[c] + ep[c]) / (ek0[c] + ep0[c]) - 1)
         assert de_g <= 2 * de_o + 1e-7, (c, de_g, de_o)
