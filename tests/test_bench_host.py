@@ -82,3 +82,46 @@ def test_reference_arm_under_torchrun_prints_from_rank_0_only():
                       "--warmup", "0", nproc=2)
     assert len(lines) == 1
     assert lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_study_jobs_and_aggregation(monkeypatch, capsys):
+    """bench.py --study: the paper's configurations become the right runs,
+    and the per-configuration summaries (worst error over the models, the
+    dynamic-vs-fixed counts and geometric mean) are formed correctly; the
+    GPU runs are replaced by a fake that returns known errors."""
+    import argparse
+    import json
+    import math
+
+    seen = []
+
+    def fake(job, span):
+        seen.append(job)
+        k = len(job["seeds"])
+        base = [1e-3 * (1 + s % 10) for s in job["seeds"]]
+        if job["era"] == "dynamic":
+            # half the fixed era's error for three models, twice for seven
+            worst = [b * (0.5 if s % 10 < 3 else 2.0)
+                     for b, s in zip(base, job["seeds"])]
+        else:
+            worst = base
+        return dict(job, worst=worst, at_end=[0.0] * k, block_steps=10 * k,
+                    seconds=0.0)
+    monkeypatch.setattr(bench, "study_job", fake)
+    args = argparse.Namespace(study_span=3, study_precision="fp64",
+                              study_workers=2)
+    assert bench.study(args) == 0
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    res = out["results"]["fp64"]
+    # Sec. 3: 5 eras x 2 pass counts (100 bodies), 7 eras (500 bodies)
+    assert len(res["sec3_n100"]) == 10 and len(res["sec3_n500"]) == 7
+    assert sum(j["n"] == 100 and j["study"] == "sec3_n100" for j in seen) == 10
+    # Sec. 4: one fixed-era ensemble of ten models + ten dynamic runs, twice
+    dyn = [j for j in seen if j["era"] == "dynamic"]
+    assert len(dyn) == 20 and all(len(j["seeds"]) == 1 for j in dyn)
+    s4 = res["sec4_n100"]
+    assert s4["models"] == 10 and s4["dynamic_at_most_fixed"] == 3
+    assert math.isclose(s4["geomean_ratio_dynamic_over_fixed"], 2.0 ** 0.4)
+    assert math.isclose(s4["worst_fixed"], 1e-2)
+    assert math.isclose(s4["worst_dynamic"], 2e-2)
+    assert out["runs"] == len(seen) == 39
