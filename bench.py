@@ -882,6 +882,9 @@ def main():
     ap.add_argument("--ensemble", action="store_true",
                     help="integrate the 512-cluster ensemble instead")
     ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--graph-steps", type=int, default=-1,
+                    help="block steps per captured graph replay (default: "
+                         "the library's)")
     ap.add_argument("--study", action="store_true",
                     help="the paper's long era / iteration study (Sec. 3-4)")
     ap.add_argument("--study-span", type=int, default=100,
@@ -944,6 +947,8 @@ def main():
     cfg.k_max = 20
     cfg.device = local
     cfg.stream = stream.cuda_stream
+    if args.graph_steps >= 0:
+        cfg.graph_steps = args.graph_steps
     ctx = tsbts.tsbts_create(cfg)
 
     def one_step(timing):
