@@ -644,6 +644,13 @@ def study(args):
                 jobs.append(dict(base, study=tag, precision=prec, n=n,
                                  eta=eta, n_iter=sec4["n_iter"],
                                  era="dynamic", seeds=[sd]))
+    if args.study_only:
+        keep = set(args.study_only.split(","))
+        jobs = [j for j in jobs if j["study"] in keep]
+    if args.study_eras:
+        eras = {float(x) for x in args.study_eras.split(",")}
+        jobs = [j for j in jobs
+                if not j["study"].startswith("sec3") or j["era"] in eras]
     # the 500-body and dynamic runs take longest: start them first
     jobs.sort(key=lambda j: (-j["n"], j["era"] != "dynamic"))
     t0 = time.perf_counter()
@@ -665,6 +672,8 @@ def study(args):
                 "worst_median": statistics.median(d["worst"]),
                 "block_steps": d["block_steps"]}
         for tag in ("sec4_n100", "sec4_n500"):
+            if not any(d["study"] == tag for d in done):
+                continue
             fixed = [d for d in done if d["precision"] == prec and
                      d["study"] == tag and d["era"] != "dynamic"][0]
             dyn = sorted((d for d in done if d["precision"] == prec and
@@ -893,6 +902,11 @@ def main():
                     choices=["both", "fp64", "mixed"])
     ap.add_argument("--study-workers", type=int, default=32,
                     help="--study: runs in flight at once")
+    ap.add_argument("--study-only", default="",
+                    help="--study: comma list of sec3_n100, sec3_n500, "
+                         "sec4_n100, sec4_n500")
+    ap.add_argument("--study-eras", default="",
+                    help="--study: comma list of the Sec. 3 era sizes to run")
     ap.add_argument("--adjoint", action="store_true",
                     help="gradient through a frozen block schedule")
     ap.add_argument("--schedule-out", default="",

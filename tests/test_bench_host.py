@@ -109,7 +109,7 @@ def test_study_jobs_and_aggregation(monkeypatch, capsys):
                     seconds=0.0)
     monkeypatch.setattr(bench, "study_job", fake)
     args = argparse.Namespace(study_span=3, study_precision="fp64",
-                              study_workers=2)
+                              study_workers=2, study_only="", study_eras="")
     assert bench.study(args) == 0
     out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     res = out["results"]["fp64"]
@@ -125,3 +125,27 @@ def test_study_jobs_and_aggregation(monkeypatch, capsys):
     assert math.isclose(s4["worst_fixed"], 1e-2)
     assert math.isclose(s4["worst_dynamic"], 2e-2)
     assert out["runs"] == len(seen) == 39
+
+
+def test_study_selection(monkeypatch, capsys):
+    import argparse
+    import json
+    seen = []
+
+    def fake(job, span):
+        seen.append(job)
+        k = len(job["seeds"])
+        return dict(job, worst=[1e-3] * k, at_end=[0.0] * k, block_steps=1,
+                    seconds=0.0)
+    monkeypatch.setattr(bench, "study_job", fake)
+    args = argparse.Namespace(study_span=2, study_precision="both",
+                              study_workers=2, study_only="sec3_n100",
+                              study_eras="0.25")
+    assert bench.study(args) == 0
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    # three and five passes at era 1/4, in both precisions
+    assert len(seen) == 4
+    assert {(j["n_iter"], j["era"], j["precision"]) for j in seen} == {
+        (3, 0.25, "fp64"), (5, 0.25, "fp64"), (3, 0.25, "mixed"),
+        (5, 0.25, "mixed")}
+    assert set(out["results"]["mixed"]) == {"sec3_n100"}
